@@ -1,0 +1,152 @@
+/*
+ * gk.h -- C ABI of the GateKeeper-GPU pre-alignment filter for sm_103a.
+ *
+ * The filter (arxiv 2103.14978) decides, for each pair of a read and a
+ * candidate reference segment of the same length m, whether the pair can be
+ * within e edits.  Per pair it builds the Hamming mask and the 2e masks of
+ * the read shifted by 1..e bases each way (Sec. 2.1), amends 0-streaks of
+ * length 1-2 bounded by 1s (Sec. 2.1), sets each shifted mask's vacated edge
+ * bits after amendment (Sec. 3.4), ANDs the 2e+1 masks and counts the errors
+ * of the result with a 4-base window table (Sec. 2.1); the pair is accepted
+ * iff the count is at most e.  Pairs whose read or window holds a base other
+ * than A/C/G/T pass without filtration (Sec. 3.3).
+ *
+ * Conventions shared by every entry point:
+ *   - return 0 (GK_OK) on success or a negative GK_E* code; the thread's last
+ *     message is in gk_last_error();
+ *   - device pointers are plain CUDA device addresses (e.g. torch tensors'
+ *     data pointers) of the current device; the library never frees memory it
+ *     did not allocate;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
+ *     enqueued asynchronously and results are valid once the stream has
+ *     reached the point of the call (the one sync point of Sec. 3.5);
+ *   - no kernel traps or spins: bad per-pair input yields a sentinel and a
+ *     counted device error, never a fault.
+ *
+ * Packed layout ("2-bit planes"): a sequence of m bases is W = ceil(m/32)
+ * words; word w is two uint32 stored adjacently, first the high bit plane
+ * then the low bit plane of the 2-bit codes A=00 C=01 G=10 T=11 (Sec. 2.1)
+ * for bases 32w..32w+31, base 32w+b in bit b.  Bits of bases >= m are 0.  A
+ * base that is not A/C/G/T (either case) is stored as 00 and flagged.
+ */
+#ifndef GK_H
+#define GK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GK_MAX_LEN 512 /* longest read / reference window, in bases */
+
+#define GK_OK 0
+#define GK_EINVAL (-1)  /* a null pointer, size or stride that cannot be right */
+#define GK_ERANGE (-2)  /* a length above GK_MAX_LEN or a count too large */
+#define GK_ENOMEM (-3)  /* a library allocation failed */
+#define GK_ECUDA (-4)   /* a CUDA call or kernel launch failed */
+
+#define GK_COUNT_RUNS4 0    /* runs of 1s per 4-base window (default) */
+#define GK_COUNT_POPCOUNT 1 /* number of 1s in the final vector */
+
+#define GK_FLAG_NO_EDGE_FIX 1u /* skip the Sec. 3.4 improvement (the original
+                                  GateKeeper), for accuracy comparisons */
+
+#define GK_EDITS_UNDEFINED 0xFFFFu /* pair holds a non-ACGT base: accept = 1 */
+#define GK_EDITS_INVALID 0xFFFEu   /* read id or window out of range: accept = 0 */
+
+typedef struct gk_ref_s *gk_ref_t;
+
+/* Message of the calling thread's last failed call ("" if none).  The
+ * pointer stays valid until that thread's next gk_* call. */
+const char *gk_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int gk_version(void);
+
+/*
+ * gk_encode -- 2-bit encoding of reads (Sec. 3.3: encode once, 16 bases per
+ * 32-bit word in the paper; here two 32-base bit planes per word pair).
+ *
+ *   ascii        n_seq sequences, sequence i starting at ascii + i*ascii_stride
+ *   ascii_stride bytes between sequence starts (>= the longest length)
+ *   lens         per-sequence lengths (uint16, each <= GK_MAX_LEN), or NULL
+ *                to use fixed_len for all
+ *   packed       output, n_seq * stride_words * 2 uint32: sequence i's word w
+ *                at packed[(i*stride_words + w)*2 + {0: high, 1: low}];
+ *                words past ceil(len/32) are zeroed
+ *   stride_words words per sequence, >= ceil(longest length / 32)
+ *   nflag        output, n_seq bytes: 1 if the sequence holds a non-ACGT
+ *                byte within its length, else 0
+ *   on_device    1: every pointer is device memory and the work is a kernel
+ *                on `stream`; 0: every pointer is host memory and the call
+ *                encodes on the host threads before returning
+ * Caller owns all buffers.  Bytes past a sequence's length are never read.
+ */
+int gk_encode(const uint8_t *ascii, uint64_t ascii_stride, const uint16_t *lens,
+              uint16_t fixed_len, uint64_t n_seq, uint32_t *packed,
+              uint32_t stride_words, uint8_t *nflag, int on_device, void *stream);
+
+/*
+ * gk_load_reference -- encode a reference genome once and keep it resident
+ * on the current device (Sec. 3.5: the reference is encoded and loaded once,
+ * and the positions of 'N' are recorded while encoding).
+ *
+ *   ascii     n_bases ASCII bytes (host memory if on_device == 0, else
+ *             device memory); n_bases < 2^32 - 2^16
+ *   out       receives the handle
+ * The handle owns device buffers of about n_bases/4 + n_bases/4 bytes (the
+ * two planes plus an N index); the call returns once they are filled.
+ * Free with gk_free_reference.  Errors: GK_EINVAL (null pointer, empty or too
+ * long reference), GK_ENOMEM, GK_ECUDA.
+ */
+int gk_load_reference(const uint8_t *ascii, uint64_t n_bases, int on_device,
+                      void *stream, gk_ref_t *out);
+
+/* Release a handle and its device buffers (NULL is ignored).  The caller
+ * guarantees no enqueued filter still reads it. */
+void gk_free_reference(gk_ref_t ref);
+
+/* Length in bases and number of non-ACGT bases of a loaded reference. */
+int gk_reference_info(gk_ref_t ref, uint64_t *n_bases, uint64_t *n_undefined);
+
+/*
+ * gk_filter -- filter n_pairs (read, candidate offset) pairs of one read
+ * length m against a loaded reference (Sec. 2.1, Sec. 3.3, Sec. 3.4; one
+ * result per pair as in Sec. 3.5).
+ *
+ *   ref          handle from gk_load_reference (same device)
+ *   reads        packed reads (device), n_reads * stride_words * 2 uint32,
+ *                as written by gk_encode
+ *   stride_words words per packed read, >= ceil(m/32)
+ *   n_reads      number of packed reads
+ *   read_nflag   device, n_reads bytes (non-zero: the read holds a non-ACGT
+ *                base), or NULL when no read does
+ *   m            read length of every pair, 0..GK_MAX_LEN
+ *   pair_read    device, n_pairs uint32 read ids
+ *   pair_off     device, n_pairs uint32 reference offsets: the segment is
+ *                bases [off, off+m) of the reference
+ *   pair_e       device, n_pairs uint8 thresholds, or NULL to use fixed_e
+ *   fixed_e      threshold for every pair when pair_e is NULL (0..255)
+ *   count_mode   GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT
+ *   flags        0 or GK_FLAG_NO_EDGE_FIX
+ *   accept_out   device, n_pairs uint8: 1 accept, 0 reject
+ *   edits_out    device, n_pairs uint16: the error count (not clamped at e),
+ *                GK_EDITS_UNDEFINED or GK_EDITS_INVALID
+ *   err_count    device uint32 or NULL: incremented once per invalid pair
+ *                (read id >= n_reads or off + m > reference length)
+ * Asynchronous on `stream`; n_pairs == 0 enqueues nothing.  Host-side
+ * argument errors return GK_EINVAL / GK_ERANGE before any work is enqueued.
+ */
+int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
+              uint64_t n_reads, const uint8_t *read_nflag, uint32_t m,
+              const uint32_t *pair_read, const uint32_t *pair_off,
+              const uint8_t *pair_e, uint32_t fixed_e, uint64_t n_pairs,
+              int count_mode, uint32_t flags, uint8_t *accept_out,
+              uint16_t *edits_out, uint32_t *err_count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GK_H */

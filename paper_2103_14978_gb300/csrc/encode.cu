@@ -1,0 +1,178 @@
+// 2-bit encoding of reads and of the reference (Sec. 3.3), device and host.
+//
+// Output layout: per 32-base word a {high plane, low plane} pair of uint32,
+// base 32w+b in bit b; the code is A=00 C=01 G=10 T=11 (Sec. 2.1).  Bytes
+// that are not A/C/G/T in either case are coded 00 and reported, per read as
+// a flag and per reference word as a bit mask (Sec. 3.3, Sec. 3.5).
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+namespace {
+
+constexpr int kTileSeqs = 64;    // reads staged in shared memory per block
+constexpr int kEncThreads = 256;
+
+// One block encodes kTileSeqs consecutive reads.  The tile's bytes are one
+// contiguous span of the input, staged into shared memory with 16-byte loads
+// where the span is aligned; each thread then builds whole words from shared
+// memory and the block ORs the undefined bits per read.
+__global__ void __launch_bounds__(kEncThreads)
+encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const uint16_t *__restrict__ lens,
+                    uint32_t fixed_len, uint64_t n_seq, uint32_t *__restrict__ packed,
+                    uint32_t stride_words, uint8_t *__restrict__ nflag) {
+  extern __shared__ __align__(16) uint8_t tile[];  // kTileSeqs * stride bytes
+  __shared__ uint32_t undef[kTileSeqs];
+  const uint64_t seq0 = (uint64_t)blockIdx.x * kTileSeqs;
+  const int nseq = (int)min_u64(kTileSeqs, n_seq - seq0);
+  const uint8_t *src = ascii + seq0 * stride;
+  if (threadIdx.x < kTileSeqs) undef[threadIdx.x] = 0;
+  // Bytes needed: up to the end of the last read's length (a length is never
+  // taken past the stride, so the tile holds at most kTileSeqs * stride).
+  const uint32_t last_len = lens ? lens[seq0 + nseq - 1] : fixed_len;
+  const uint64_t need = (uint64_t)(nseq - 1) * stride + min_u64(last_len, stride);
+  const bool aligned = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+  if (aligned) {
+    const uint64_t n16 = need / 16;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *t4 = reinterpret_cast<uint4 *>(tile);
+    for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) t4[i] = s4[i];
+    for (uint64_t i = n16 * 16 + threadIdx.x; i < need; i += blockDim.x) tile[i] = src[i];
+  } else {
+    for (uint64_t i = threadIdx.x; i < need; i += blockDim.x) tile[i] = src[i];
+  }
+  __syncthreads();
+  const int total = nseq * (int)stride_words;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int s = t / (int)stride_words;
+    const int w = t - s * (int)stride_words;
+    const uint32_t len = (uint32_t)min_u64(lens ? lens[seq0 + s] : fixed_len, stride);
+    uint32_t hi = 0, lo = 0, nb = 0;
+    const int b0 = w * 32;
+    const int nb_here = (int)min_i64(32, (int64_t)len - b0);
+    const uint8_t *p = tile + (uint64_t)s * stride + b0;
+    for (int b = 0; b < nb_here; ++b) {
+      uint32_t h, l, u;
+      code_of(p[b], h, l, u);
+      hi |= h << b;
+      lo |= l << b;
+      nb |= u;
+    }
+    uint32_t *out = packed + ((seq0 + s) * (uint64_t)stride_words + w) * 2;
+    *reinterpret_cast<uint2 *>(out) = make_uint2(hi, lo);
+    if (nb) atomicOr(&undef[s], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < nseq) nflag[seq0 + threadIdx.x] = (uint8_t)(undef[threadIdx.x] != 0);
+}
+
+// One thread per 32-base word of a contiguous sequence (the reference): two
+// 16-byte loads when the word is complete, byte loads for the tail word.
+__global__ void encode_contig_kernel(const uint8_t *__restrict__ ascii, uint64_t n_bases,
+                                     uint2 *__restrict__ hl, uint32_t *__restrict__ nbits,
+                                     uint64_t n_words) {
+  const uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (w >= n_words) return;
+  const uint64_t b0 = w * 32;
+  uint32_t hi = 0, lo = 0, nb = 0;
+  if (b0 + 32 <= n_bases && (reinterpret_cast<uintptr_t>(ascii) & 15u) == 0) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(ascii + b0);
+    uint4 v[2] = {s4[0], s4[1]};
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t h, l, u;
+        code_of((words[q] >> (8 * j)) & 0xFFu, h, l, u);
+        const int b = q * 4 + j;
+        hi |= h << b;
+        lo |= l << b;
+        nb |= u << b;
+      }
+    }
+  } else {
+    const int n = (int)min_u64(32, n_bases - b0);
+    for (int b = 0; b < n; ++b) {
+      uint32_t h, l, u;
+      code_of(ascii[b0 + b], h, l, u);
+      hi |= h << b;
+      lo |= l << b;
+      nb |= u << b;
+    }
+  }
+  hl[w] = make_uint2(hi, lo);
+  nbits[w] = nb;
+}
+
+}  // namespace
+
+cudaError_t launch_encode_reads(const uint8_t *ascii, uint64_t ascii_stride, const uint16_t *lens,
+                                uint16_t fixed_len, uint64_t n_seq, uint32_t *packed,
+                                uint32_t stride_words, uint8_t *nflag, cudaStream_t stream) {
+  if (n_seq == 0) return cudaSuccess;
+  const uint64_t blocks = (n_seq + kTileSeqs - 1) / kTileSeqs;
+  const size_t smem = (size_t)kTileSeqs * ascii_stride + 16;
+  if (smem > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(encode_reads_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  encode_reads_kernel<<<(unsigned)blocks, kEncThreads, smem, stream>>>(
+      ascii, ascii_stride, lens, fixed_len, n_seq, packed, stride_words, nflag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_contig(const uint8_t *ascii, uint64_t n_bases, uint2 *hl, uint32_t *nbits,
+                                 cudaStream_t stream) {
+  const uint64_t n_words = (n_bases + 31) / 32;
+  if (n_words == 0) return cudaSuccess;
+  const int threads = 256;
+  encode_contig_kernel<<<(unsigned)((n_words + threads - 1) / threads), threads, 0, stream>>>(
+      ascii, n_bases, hl, nbits, n_words);
+  return cudaGetLastError();
+}
+
+void host_encode_reads(const uint8_t *ascii, uint64_t ascii_stride, const uint16_t *lens,
+                       uint16_t fixed_len, uint64_t n_seq, uint32_t *packed, uint32_t stride_words,
+                       uint8_t *nflag) {
+  auto work = [&](uint64_t lo_seq, uint64_t hi_seq) {
+    for (uint64_t s = lo_seq; s < hi_seq; ++s) {
+      const uint32_t len = (uint32_t)std::min<uint64_t>(lens ? lens[s] : fixed_len, ascii_stride);
+      const uint8_t *p = ascii + s * ascii_stride;
+      uint32_t any = 0;
+      for (uint32_t w = 0; w < stride_words; ++w) {
+        uint32_t hi = 0, lo = 0;
+        for (uint32_t b = 0; b < 32 && w * 32 + b < len; ++b) {
+          uint32_t h, l, u;
+          code_of(p[w * 32 + b], h, l, u);
+          hi |= h << b;
+          lo |= l << b;
+          any |= u;
+        }
+        uint32_t *out = packed + (s * stride_words + w) * 2;
+        out[0] = hi;
+        out[1] = lo;
+      }
+      nflag[s] = (uint8_t)(any != 0);
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const uint64_t nthreads = std::min<uint64_t>(hw, std::max<uint64_t>(1, n_seq / 4096));
+  if (nthreads <= 1) {
+    work(0, n_seq);
+    return;
+  }
+  std::vector<std::thread> pool;
+  const uint64_t chunk = (n_seq + nthreads - 1) / nthreads;
+  for (uint64_t t = 0; t < nthreads; ++t) {
+    const uint64_t a = std::min(n_seq, t * chunk), b = std::min(n_seq, a + chunk);
+    pool.emplace_back(work, a, b);
+  }
+  for (auto &th : pool) th.join();
+}
+
+}  // namespace gk

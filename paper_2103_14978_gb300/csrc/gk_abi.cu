@@ -1,0 +1,240 @@
+// C ABI of libgk: argument checks, error reporting, the resident reference
+// and the launch of the filter kernels.  Declarations and contracts are in
+// include/gk.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+cudaError_t launch_filter_w1_4(int W, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w5_8(int W, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w9_12(int W, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w13_16(int W, const FilterArgs &a, cudaStream_t stream);
+
+namespace {
+thread_local std::string t_last_error;
+}
+
+int fail(int code, const std::string &msg) {
+  t_last_error = msg;
+  return code;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+int cuda_check(cudaError_t err, const char *what) {
+  if (err == cudaSuccess) return GK_OK;
+  return fail(GK_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
+  if (W >= 1 && W <= 4) return launch_filter_w1_4(W, a, stream);
+  if (W <= 8) return launch_filter_w5_8(W, a, stream);
+  if (W <= 12) return launch_filter_w9_12(W, a, stream);
+  if (W <= 16) return launch_filter_w13_16(W, a, stream);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gk
+
+using gk::fail;
+
+namespace {
+
+constexpr uint64_t kMaxRefBases = (1ull << 32) - (1ull << 16);
+constexpr uint64_t kMaxPairs = (1ull << 31) * 128ull;  // grid x limit at 256 threads
+constexpr uint64_t kMaxDeviceAsciiStride = 3072;      // encoder tile: 64 reads in shared memory
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+struct DeviceBuffer {
+  void *p = nullptr;
+  ~DeviceBuffer() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *gk_last_error(void) { return gk::t_last_error.c_str(); }
+
+int gk_version(void) { return 100; }  // 0.1.0
+
+int gk_encode(const uint8_t *ascii, uint64_t ascii_stride, const uint16_t *lens,
+              uint16_t fixed_len, uint64_t n_seq, uint32_t *packed, uint32_t stride_words,
+              uint8_t *nflag, int on_device, void *stream) {
+  gk::clear_error();
+  if (n_seq == 0) return GK_OK;
+  if (!ascii || !packed || !nflag) return fail(GK_EINVAL, "gk_encode: null buffer");
+  if (!lens && fixed_len > GK_MAX_LEN)
+    return fail(GK_ERANGE, "gk_encode: fixed_len above GK_MAX_LEN");
+  if (!lens && fixed_len > ascii_stride)
+    return fail(GK_EINVAL, "gk_encode: fixed_len larger than ascii_stride");
+  if (stride_words == 0 || stride_words > GK_MAX_LEN / 32)
+    return fail(GK_EINVAL, "gk_encode: stride_words must be 1..GK_MAX_LEN/32");
+  if (!lens && (uint32_t)fixed_len > 32u * stride_words)
+    return fail(GK_EINVAL, "gk_encode: stride_words too small for fixed_len");
+  if (ascii_stride == 0) return fail(GK_EINVAL, "gk_encode: ascii_stride is 0");
+  if (!aligned(packed, 8)) return fail(GK_EINVAL, "gk_encode: packed must be 8-byte aligned");
+  if (on_device) {
+    if (ascii_stride > kMaxDeviceAsciiStride)
+      return fail(GK_ERANGE, "gk_encode: device path needs ascii_stride <= 3072");
+    cudaError_t err = gk::launch_encode_reads(ascii, ascii_stride, lens, fixed_len, n_seq, packed,
+                                              stride_words, nflag, (cudaStream_t)stream);
+    return gk::cuda_check(err, "gk_encode: launch");
+  }
+  gk::host_encode_reads(ascii, ascii_stride, lens, fixed_len, n_seq, packed, stride_words, nflag);
+  return GK_OK;
+}
+
+int gk_load_reference(const uint8_t *ascii, uint64_t n_bases, int on_device, void *stream,
+                      gk_ref_t *out) {
+  gk::clear_error();
+  if (!ascii || !out) return fail(GK_EINVAL, "gk_load_reference: null pointer");
+  *out = nullptr;
+  if (n_bases == 0 || n_bases >= kMaxRefBases)
+    return fail(GK_EINVAL, "gk_load_reference: n_bases must be in 1..2^32-2^16");
+  cudaStream_t s = (cudaStream_t)stream;
+  gk_ref_s *ref = new (std::nothrow) gk_ref_s();
+  if (!ref) return fail(GK_ENOMEM, "gk_load_reference: host allocation");
+  int rc = GK_OK;
+  const uint64_t n_words = (n_bases + 31) / 32;
+  ref->n_bases = n_bases;
+  ref->n_words = n_words;
+  cudaGetDevice(&ref->device);
+  DeviceBuffer staging, nbits_dev;
+  std::vector<uint32_t> nbits;
+  std::vector<uint2> nidx;
+  const uint8_t *dev_ascii = ascii;
+  do {
+    if (cudaMalloc(&ref->hl, (n_words + 2) * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&nbits_dev.p, (n_words + 2) * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(GK_ENOMEM, "gk_load_reference: device allocation");
+      break;
+    }
+    if (!on_device) {
+      if (cudaMalloc(&staging.p, n_bases) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(GK_ENOMEM, "gk_load_reference: device staging allocation");
+        break;
+      }
+      rc = gk::cuda_check(cudaMemcpyAsync(staging.p, ascii, n_bases, cudaMemcpyHostToDevice, s),
+                          "gk_load_reference: copy to device");
+      if (rc) break;
+      dev_ascii = static_cast<const uint8_t *>(staging.p);
+    }
+    rc = gk::cuda_check(cudaMemsetAsync(ref->hl, 0, (n_words + 2) * sizeof(uint2), s),
+                        "gk_load_reference: memset");
+    if (rc) break;
+    rc = gk::cuda_check(gk::launch_encode_contig(dev_ascii, n_bases, ref->hl,
+                                                 static_cast<uint32_t *>(nbits_dev.p), s),
+                        "gk_load_reference: encode");
+    if (rc) break;
+    // The N index: per word its N bits and the first N position at or after
+    // the next word, so that one load answers "any N in [off, off+m)".
+    nbits.resize(n_words);
+    rc = gk::cuda_check(cudaMemcpyAsync(nbits.data(), nbits_dev.p, n_words * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, s),
+                        "gk_load_reference: copy N bits");
+    if (rc) break;
+    rc = gk::cuda_check(cudaStreamSynchronize(s), "gk_load_reference: synchronize");
+    if (rc) break;
+    uint64_t n_undef = 0;
+    for (uint64_t w = 0; w < n_words; ++w) n_undef += (uint64_t)__builtin_popcount(nbits[w]);
+    ref->n_undefined = n_undef;
+    if (n_undef > 0) {
+      nidx.resize(n_words + 2);
+      uint32_t next = 0xffffffffu;  // first N position >= 32*(w+1)
+      nidx[n_words] = make_uint2(0, next);
+      nidx[n_words + 1] = make_uint2(0, next);
+      for (uint64_t w = n_words; w-- > 0;) {
+        nidx[w] = make_uint2(nbits[w], next);
+        if (nbits[w]) next = (uint32_t)(32 * w + (uint64_t)__builtin_ctz(nbits[w]));
+      }
+      if (cudaMalloc(&ref->nidx, (n_words + 2) * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(GK_ENOMEM, "gk_load_reference: N index allocation");
+        break;
+      }
+      rc = gk::cuda_check(cudaMemcpyAsync(ref->nidx, nidx.data(), (n_words + 2) * sizeof(uint2),
+                                          cudaMemcpyHostToDevice, s),
+                          "gk_load_reference: copy N index");
+      if (rc) break;
+    }
+    rc = gk::cuda_check(cudaStreamSynchronize(s), "gk_load_reference: synchronize");
+  } while (false);
+  if (rc != GK_OK) {
+    gk_free_reference(ref);
+    return rc;
+  }
+  *out = ref;
+  return GK_OK;
+}
+
+void gk_free_reference(gk_ref_t ref) {
+  if (!ref) return;
+  if (ref->hl) cudaFree(ref->hl);
+  if (ref->nidx) cudaFree(ref->nidx);
+  delete ref;
+}
+
+int gk_reference_info(gk_ref_t ref, uint64_t *n_bases, uint64_t *n_undefined) {
+  gk::clear_error();
+  if (!ref) return fail(GK_EINVAL, "gk_reference_info: null handle");
+  if (n_bases) *n_bases = ref->n_bases;
+  if (n_undefined) *n_undefined = ref->n_undefined;
+  return GK_OK;
+}
+
+int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64_t n_reads,
+              const uint8_t *read_nflag, uint32_t m, const uint32_t *pair_read,
+              const uint32_t *pair_off, const uint8_t *pair_e, uint32_t fixed_e,
+              uint64_t n_pairs, int count_mode, uint32_t flags, uint8_t *accept_out,
+              uint16_t *edits_out, uint32_t *err_count, void *stream) {
+  gk::clear_error();
+  if (!ref) return fail(GK_EINVAL, "gk_filter: null reference handle");
+  if (m > GK_MAX_LEN) return fail(GK_ERANGE, "gk_filter: m above GK_MAX_LEN");
+  if (n_pairs == 0) return GK_OK;
+  if (n_pairs > kMaxPairs) return fail(GK_ERANGE, "gk_filter: too many pairs for one launch");
+  if (!pair_read || !pair_off || !accept_out || !edits_out)
+    return fail(GK_EINVAL, "gk_filter: null pair or output buffer");
+  const uint32_t W = m == 0 ? 1 : (m + 31) / 32;
+  if (m > 0 && (!reads || stride_words < W))
+    return fail(GK_EINVAL, "gk_filter: reads missing or stride_words < ceil(m/32)");
+  if (!pair_e && fixed_e > 255) return fail(GK_ERANGE, "gk_filter: fixed_e above 255");
+  if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
+    return fail(GK_EINVAL, "gk_filter: unknown count_mode");
+  if (flags & ~GK_FLAG_NO_EDGE_FIX) return fail(GK_EINVAL, "gk_filter: unknown flags");
+  if (reads && !aligned(reads, 8)) return fail(GK_EINVAL, "gk_filter: reads must be 8-byte aligned");
+  gk::FilterArgs a{};
+  a.ref_hl = ref->hl;
+  a.ref_nidx = ref->nidx;
+  a.ref_len = ref->n_bases;
+  a.reads = reinterpret_cast<const uint2 *>(reads);
+  a.stride_words = stride_words;
+  a.n_reads = n_reads;
+  a.read_nflag = read_nflag;
+  a.m = m;
+  a.pair_read = pair_read;
+  a.pair_off = pair_off;
+  a.pair_e = pair_e;
+  a.fixed_e = fixed_e;
+  a.n_pairs = n_pairs;
+  a.count_mode = count_mode;
+  a.edge_on = (flags & GK_FLAG_NO_EDGE_FIX) ? 0 : 1;
+  a.accept = accept_out;
+  a.edits = edits_out;
+  a.err_count = err_count;
+  return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
+}
+
+}  // extern "C"

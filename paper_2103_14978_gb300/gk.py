@@ -1,0 +1,217 @@
+"""Python binding of libgk (include/gk.h): argument marshalling only.
+
+Every function forwards to the C entry point of the same name; all filter
+work runs in the library's CUDA kernels.  Device buffers are torch tensors,
+streams are torch streams.  There is no fallback: if libgk.so is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+GK_MAX_LEN = 512
+GK_OK, GK_EINVAL, GK_ERANGE, GK_ENOMEM, GK_ECUDA = 0, -1, -2, -3, -4
+GK_COUNT_RUNS4, GK_COUNT_POPCOUNT = 0, 1
+GK_FLAG_NO_EDGE_FIX = 1
+GK_EDITS_UNDEFINED, GK_EDITS_INVALID = 0xFFFF, 0xFFFE
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgk.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_c = ctypes
+_SIGS = {
+    "gk_last_error": ([], _c.c_char_p),
+    "gk_version": ([], _c.c_int),
+    "gk_encode": ([_c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_uint16, _c.c_uint64, _c.c_void_p,
+                   _c.c_uint32, _c.c_void_p, _c.c_int, _c.c_void_p], _c.c_int),
+    "gk_load_reference": ([_c.c_void_p, _c.c_uint64, _c.c_int, _c.c_void_p, _c.POINTER(_c.c_void_p)],
+                          _c.c_int),
+    "gk_free_reference": ([_c.c_void_p], None),
+    "gk_reference_info": ([_c.c_void_p, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)], _c.c_int),
+    "gk_filter": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_uint32,
+                   _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
+                   _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_probe_alu": ([_c.c_int, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_void_p, _c.c_void_p], _c.c_int),
+}
+
+
+class GKError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libgk error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgk.so.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != GK_OK:
+        raise GKError(rc, lib().gk_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t: torch.Tensor | None, dtype: torch.dtype, name: str, numel: int | None = None) -> int | None:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+def words_for(m: int) -> int:
+    return max(1, -(-int(m) // 32))
+
+
+class Reference:
+    """A reference genome encoded once and resident on the current device."""
+
+    def __init__(self, handle: int, n_bases: int, n_undefined: int, device: int):
+        self.handle = handle
+        self.n_bases = n_bases
+        self.n_undefined = n_undefined
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            gk_free_reference(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gk_load_reference(ascii, stream=None) -> Reference:
+    """Encode ``ascii`` (a uint8 numpy array / host tensor, or a CUDA uint8
+    tensor) and keep it resident (gk_load_reference)."""
+    if isinstance(ascii, np.ndarray):
+        ascii = torch.from_numpy(np.ascontiguousarray(ascii, dtype=np.uint8))
+    if ascii.dtype != torch.uint8 or not ascii.is_contiguous():
+        raise TypeError("reference must be a contiguous uint8 array")
+    h = ctypes.c_void_p()
+    _check(lib().gk_load_reference(ascii.data_ptr(), ascii.numel(), 1 if ascii.is_cuda else 0,
+                                   _stream(stream), ctypes.byref(h)))
+    nb, nu = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().gk_reference_info(h, ctypes.byref(nb), ctypes.byref(nu)))
+    return Reference(h.value, nb.value, nu.value, torch.cuda.current_device())
+
+
+def gk_free_reference(ref: Reference):
+    lib().gk_free_reference(ref.handle)
+
+
+def gk_encode(ascii: torch.Tensor, n_seq: int, ascii_stride: int, lens: torch.Tensor | None = None,
+              fixed_len: int = 0, stride_words: int | None = None, packed: torch.Tensor | None = None,
+              nflag: torch.Tensor | None = None, stream=None):
+    """2-bit planes of n_seq sequences (gk_encode).  Device tensors run the
+    device encoder on ``stream``; host tensors run the host encoder.  Returns
+    (packed int32 [n_seq * stride_words * 2], nflag uint8 [n_seq])."""
+    on_device = ascii.is_cuda
+    if stride_words is None:
+        stride_words = words_for(fixed_len if lens is None else GK_MAX_LEN)
+    dev = ascii.device
+    if packed is None:
+        packed = torch.empty(n_seq * stride_words * 2, dtype=torch.int32, device=dev)
+    if nflag is None:
+        nflag = torch.empty(n_seq, dtype=torch.uint8, device=dev)
+    for t, name in ((packed, "packed"), (nflag, "nflag")) + (((lens, "lens"),) if lens is not None else ()):
+        if t.is_cuda != on_device:
+            raise TypeError(f"{name} must live where ascii lives")
+    if not ascii.is_contiguous() or ascii.dtype != torch.uint8:
+        raise TypeError("ascii must be contiguous uint8")
+    need = (n_seq - 1) * ascii_stride + (fixed_len if lens is None else ascii_stride)
+    if n_seq and ascii.numel() < need:
+        raise ValueError("ascii is shorter than n_seq sequences")
+    if packed.numel() < n_seq * stride_words * 2 or nflag.numel() < n_seq:
+        raise ValueError("output buffers too small")
+    if lens is not None and (lens.dtype != torch.int16 or lens.numel() < n_seq):
+        raise TypeError("lens must hold n_seq int16 (read as uint16) lengths")
+    _check(lib().gk_encode(ascii.data_ptr(), ascii_stride, lens.data_ptr() if lens is not None else None,
+                           fixed_len, n_seq, packed.data_ptr(), stride_words, nflag.data_ptr(),
+                           1 if on_device else 0, _stream(stream) if on_device else None))
+    return packed, nflag
+
+
+def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: int,
+              read_nflag: torch.Tensor | None, m: int, pair_read: torch.Tensor, pair_off: torch.Tensor,
+              e, count_mode: int = GK_COUNT_RUNS4, flags: int = 0, accept: torch.Tensor | None = None,
+              edits: torch.Tensor | None = None, err_count: torch.Tensor | None = None, stream=None):
+    """Filter pairs of read length m (gk_filter).  ``e`` is an int or a CUDA
+    uint8 tensor (one threshold per pair).  ``pair_read``/``pair_off`` are
+    int32 CUDA tensors read as uint32.  Returns (accept uint8, edits int16 read
+    as uint16)."""
+    n = pair_read.numel()
+    dev = pair_read.device
+    if accept is None:
+        accept = torch.empty(n, dtype=torch.uint8, device=dev)
+    if edits is None:
+        edits = torch.empty(n, dtype=torch.int16, device=dev)
+    if m > 0 and reads.numel() < n_reads * stride_words * 2:
+        raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
+    pe = None
+    fixed_e = 0
+    if isinstance(e, torch.Tensor):
+        pe = _dptr(e, torch.uint8, "e", n)
+    else:
+        fixed_e = int(e)
+    _check(lib().gk_filter(
+        ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
+        _dptr(read_nflag, torch.uint8, "read_nflag", n_reads), m,
+        _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n),
+        pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
+        _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1),
+        _stream(stream)))
+    return accept, edits
+
+
+GK_PROBE_LOP3, GK_PROBE_SHF, GK_PROBE_MIX = 0, 1, 2
+
+
+def gk_probe_alu(kind: int, iters: int, blocks: int, threads: int, sink: torch.Tensor, stream=None):
+    """Enqueue the integer-throughput probe (include/gk_probe.h); issues
+    blocks * threads * iters * 64 ops."""
+    _check(lib().gk_probe_alu(kind, iters, blocks, threads, _dptr(sink, torch.int32, "sink", 1),
+                              _stream(stream)))
+
+
+def version() -> int:
+    return lib().gk_version()
