@@ -51,13 +51,15 @@ L2_BYTES = 129 * 1024 * 1024
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the 20M-pair workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--es", default="0-10", help="thresholds of the sweep, e.g. 0-10 or 2,10")
+    ap.add_argument("--probe-all", action="store_true", help="run every integer probe kind")
     return ap.parse_args()
 
 
@@ -235,13 +237,18 @@ def run_reference(args):
 
 # ---- the GPU arm ---------------------------------------------------------------
 
-def probe_alu(torch, gk, stream):
+def probe_alu(torch, gk, stream, every=False):
     """Measured integer issue rate of the filter's mix (ops/s)."""
     sink = torch.zeros(1, dtype=torch.int32, device="cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks, threads, iters = sms * 8, 256, 4096
     out = {}
-    for kind, name in ((gk.GK_PROBE_LOP3, "lop3"), (gk.GK_PROBE_SHF, "shf"), (gk.GK_PROBE_MIX, "mix")):
+    kinds = [(0, "lop3"), (1, "shf"), (2, "mix")]
+    if every:
+        kinds += [(3, "imad"), (4, "lop3+imad"), (5, "iadd"), (6, "lop3+iadd"), (7, "shf+imad"),
+                  (8, "addc"), (9, "lop3+addc"), (10, "wide"), (11, "lop3+wide"), (12, "lop3x3+wide"),
+                  (13, "mulhi+lop3"), (14, "funnel_fma+lop3")]
+    for kind, name in kinds:
         gk.gk_probe_alu(kind, 64, blocks, threads, sink, stream)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
@@ -339,7 +346,7 @@ def run_mine(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    probe = probe_alu(torch, gk, stream)
+    probe = probe_alu(torch, gk, stream, args.probe_all)
 
     e2e = None
     if not args.no_e2e:
@@ -435,8 +442,21 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
                                           "11 x gk_filter -> results to pinned host"}
 
 
+def parse_es(spec: str):
+    out = []
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            out += list(range(int(a), int(b) + 1))
+        else:
+            out.append(int(part))
+    return out
+
+
 def main():
+    global E_SWEEP
     args = parse_args()
+    E_SWEEP = parse_es(args.es)
     if args.impl == "reference":
         run_reference(args)
     else:

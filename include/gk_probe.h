@@ -19,6 +19,18 @@ extern "C" {
 #define GK_PROBE_LOP3 0  /* 3-input logic ops */
 #define GK_PROBE_SHF 1   /* funnel shifts */
 #define GK_PROBE_MIX 2   /* the filter's mix: ~1 funnel shift per logic op */
+#define GK_PROBE_IMAD 3  /* integer multiply-add (runtime multiplier) */
+#define GK_PROBE_LOP3_IMAD 4 /* logic ops and multiply-adds, one to one */
+#define GK_PROBE_IADD 5  /* integer adds */
+#define GK_PROBE_LOP3_IADD 6 /* logic ops and adds, one to one */
+#define GK_PROBE_SHF_IMAD 7  /* funnel shifts and multiply-adds, one to one */
+#define GK_PROBE_ADDC 8      /* 4-word add-with-carry chains (x + x: shift by 1) */
+#define GK_PROBE_LOP3_ADDC 9 /* logic ops and add-with-carry, one to one */
+#define GK_PROBE_WIDE 10     /* 32x32->64 multiply-adds */
+#define GK_PROBE_LOP3_WIDE 11 /* logic ops and wide multiply-adds, one to one */
+#define GK_PROBE_LOP3_WIDE_2 12 /* logic ops and wide multiply-adds, two to one */
+#define GK_PROBE_MULHI 13    /* high half of 32x32 products */
+#define GK_PROBE_FUNNEL_FMA 14 /* funnel shift as mad.hi + mad.lo, mixed 1:1 with logic ops */
 
 /*
  * Launches `blocks` x `threads` threads, each running `iters` iterations of

@@ -19,6 +19,43 @@ __device__ __forceinline__ uint32_t shf_l(uint32_t lo, uint32_t hi, uint32_t n) 
   return d;
 }
 
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t iadd(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm volatile("add.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// 4-word vector doubled in place: a multi-word shift left by one bit.
+__device__ __forceinline__ void addc4(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d) {
+  asm volatile(
+      "add.cc.u32 %0, %0, %0;\n\t"
+      "addc.cc.u32 %1, %1, %1;\n\t"
+      "addc.cc.u32 %2, %2, %2;\n\t"
+      "addc.u32 %3, %3, %3;"
+      : "+r"(a), "+r"(b), "+r"(c), "+r"(d));
+}
+
+__device__ __forceinline__ void wide(uint32_t &lo, uint32_t &hi, uint32_t k) {
+  asm volatile(
+      "{\n\t.reg .u64 t, acc;\n\t"
+      "mov.b64 acc, {%0, %1};\n\t"
+      "mad.wide.u32 t, %0, %2, acc;\n\t"
+      "mov.b64 {%0, %1}, t;\n\t}"
+      : "+r"(lo), "+r"(hi) : "r"(k));
+}
+
+__device__ __forceinline__ uint32_t mulhi(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
 template <int KIND>
 __global__ void probe_kernel(uint32_t iters, uint32_t seed, uint32_t *sink) {
   constexpr int kChains = 16;
@@ -35,9 +72,52 @@ __global__ void probe_kernel(uint32_t iters, uint32_t seed, uint32_t *sink) {
           x[i] = lop3_xor_or(x[i], k1, k2 + r);
         } else if (KIND == GK_PROBE_SHF) {
           x[i] = shf_l(x[(i + 1) % kChains], x[i], sh);
-        } else {
+        } else if (KIND == GK_PROBE_MIX) {
           x[i] = (r & 1) ? shf_l(x[(i + 1) % kChains], x[i], sh) : lop3_xor_or(x[i], k1, k2);
+        } else if (KIND == GK_PROBE_IMAD) {
+          x[i] = imad(x[i], k1, k2 + r);
+        } else if (KIND == GK_PROBE_LOP3_IMAD) {
+          x[i] = (i & 1) ? imad(x[i], k1, k2) : lop3_xor_or(x[i], k1, k2 + r);
+        } else if (KIND == GK_PROBE_IADD) {
+          x[i] = iadd(x[i], k2 + r);
+        } else if (KIND == GK_PROBE_LOP3_IADD) {
+          x[i] = (i & 1) ? iadd(x[i], k2 + r) : lop3_xor_or(x[i], k1, k2 + r);
+        } else if (KIND == GK_PROBE_SHF_IMAD) {
+          x[i] = (i & 1) ? imad(x[i], k1, k2) : shf_l(x[(i + 1) % kChains], x[i], sh);
         }
+      }
+      if (KIND == GK_PROBE_ADDC) {
+#pragma unroll
+        for (int i = 0; i < kChains; i += 4) addc4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+      } else if (KIND == GK_PROBE_LOP3_ADDC) {
+#pragma unroll
+        for (int i = 0; i < kChains / 2; i += 4) addc4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+#pragma unroll
+        for (int i = kChains / 2; i < kChains; ++i) x[i] = lop3_xor_or(x[i], k1, k2 + r);
+      } else if (KIND == GK_PROBE_WIDE) {
+#pragma unroll
+        for (int i = 0; i < kChains; i += 2) wide(x[i], x[i + 1], k1);
+      } else if (KIND == GK_PROBE_LOP3_WIDE) {
+#pragma unroll
+        for (int i = 0; i < kChains / 2; i += 2) wide(x[i], x[i + 1], k1);
+#pragma unroll
+        for (int i = kChains / 2; i < kChains; ++i) x[i] = lop3_xor_or(x[i], k1, k2 + r);
+      } else if (KIND == GK_PROBE_MULHI) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) x[i] = mulhi(x[i], k1) ^ x[i];
+      } else if (KIND == GK_PROBE_FUNNEL_FMA) {
+        // 4 funnel shifts (8 multiply ops) and 8 logic ops per round
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) x[i] = imad(x[i], k1, mulhi(x[i + 1], k1));
+#pragma unroll
+        for (int i = 8; i < kChains; ++i) x[i] = lop3_xor_or(x[i], k1, k2 + r);
+#pragma unroll
+        for (int i = 1; i < 8; i += 2) x[i] = lop3_xor_or(x[i], x[i - 1], k2);
+      } else if (KIND == GK_PROBE_LOP3_WIDE_2) {
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) wide(x[i], x[i + 1], k1);
+#pragma unroll
+        for (int i = 4; i < kChains; ++i) x[i] = lop3_xor_or(x[i], k1, k2 + r);
       }
     }
   }
@@ -59,6 +139,18 @@ extern "C" int gk_probe_alu(int kind, uint32_t iters, uint32_t blocks, uint32_t 
     case GK_PROBE_LOP3: probe_kernel<GK_PROBE_LOP3><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
     case GK_PROBE_SHF: probe_kernel<GK_PROBE_SHF><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
     case GK_PROBE_MIX: probe_kernel<GK_PROBE_MIX><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_IMAD: probe_kernel<GK_PROBE_IMAD><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_LOP3_IMAD: probe_kernel<GK_PROBE_LOP3_IMAD><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_IADD: probe_kernel<GK_PROBE_IADD><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_LOP3_IADD: probe_kernel<GK_PROBE_LOP3_IADD><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_SHF_IMAD: probe_kernel<GK_PROBE_SHF_IMAD><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_ADDC: probe_kernel<GK_PROBE_ADDC><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_LOP3_ADDC: probe_kernel<GK_PROBE_LOP3_ADDC><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_WIDE: probe_kernel<GK_PROBE_WIDE><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_LOP3_WIDE: probe_kernel<GK_PROBE_LOP3_WIDE><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_LOP3_WIDE_2: probe_kernel<GK_PROBE_LOP3_WIDE_2><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_MULHI: probe_kernel<GK_PROBE_MULHI><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
+    case GK_PROBE_FUNNEL_FMA: probe_kernel<GK_PROBE_FUNNEL_FMA><<<blocks, threads, 0, s>>>(iters, 0x1234567u, sink); break;
     default: return gk::fail(GK_EINVAL, "gk_probe_alu: unknown kind");
   }
   return gk::cuda_check(cudaGetLastError(), "gk_probe_alu: launch");

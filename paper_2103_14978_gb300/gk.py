@@ -124,7 +124,10 @@ def gk_load_reference(ascii, stream=None) -> Reference:
     """Encode ``ascii`` (a uint8 numpy array / host tensor, or a CUDA uint8
     tensor) and keep it resident (gk_load_reference)."""
     if isinstance(ascii, np.ndarray):
-        ascii = torch.from_numpy(np.ascontiguousarray(ascii, dtype=np.uint8))
+        ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+        if not ascii.flags.writeable:
+            ascii = ascii.copy()
+        ascii = torch.from_numpy(ascii)
     if ascii.dtype != torch.uint8 or not ascii.is_contiguous():
         raise TypeError("reference must be a contiguous uint8 array")
     h = ctypes.c_void_p()

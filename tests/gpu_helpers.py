@@ -28,7 +28,9 @@ class GpuRun:
         self.m = int(lens[0])
 
     def filter(self, e=None, mode=gk.GK_COUNT_RUNS4, flags=0, err=None, stream=None):
-        ee = self.pairs.pair_e if e is None else e
+        if e is None:
+            e = self.pairs.pair_e if self.pairs.pair_e is not None else self.w.e
+        ee = e
         acc, ed = gk.gk_filter(self.ref, self.reads.packed, self.reads.stride_words, self.reads.n_reads,
                                self.reads.nflag, self.m, self.pairs.pair_read, self.pairs.pair_off, ee,
                                count_mode=mode, flags=flags, err_count=err, stream=stream)
@@ -38,7 +40,9 @@ class GpuRun:
 
 def oracle_run(w: synth.Workload, e=None, mode=O.RUNS4, flags=0, idx=None):
     pr, po = w.pair_read, w.pair_off
-    pe = w.pair_e if e is None else e
+    if e is None:
+        e = w.pair_e if w.pair_e is not None else w.e
+    pe = e
     if idx is not None:
         pr, po = pr[idx], po[idx]
         if not np.isscalar(pe) and pe is not None:
@@ -58,7 +62,9 @@ def assert_same(got, want, what=""):
 
 
 def small_workload(m: int, n_pairs: int, seed: int, ref_len: int = 200_000, n_frac: float = 0.0,
-                   read_n_frac: float = 0.0, cands=4, e=0, e_rates=None, read_edit_rate=0.04):
+                   read_n_frac: float = 0.0, cands=4, e=None, e_rates=None, read_edit_rate=0.04):
+    if e is None and e_rates is None:
+        e = 0
     ref = synth.reference(ref_len, seed, 0.05, n_frac)
     return synth.pairs_workload(f"small-m{m}", seed=seed, ref=ref, n_pairs=n_pairs, m=m, cands=cands,
                                 e=e, e_rates=e_rates, read_edit_rate=read_edit_rate,
