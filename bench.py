@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--es", default="0-10", help="thresholds of the sweep, e.g. 0-10 or 2,10")
     ap.add_argument("--probe-all", action="store_true", help="run every integer probe kind")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: the default line; c3: 150/250 bp with N; c4: batched mixed lengths")
+    ap.add_argument("--tune-seconds", type=float, default=60.0, help="autotuner budget (config 4)")
     return ap.parse_args()
 
 
@@ -453,12 +456,150 @@ def parse_es(spec: str):
     return out
 
 
+def time_events(torch, fn, steps, stream):
+    """Mean ms of fn() over `steps` calls, CUDA events on `stream`."""
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def run_config3(args):
+    """Config 3: 10M pairs at 150 bp (e 0..15) and 250 bp (e 0..25), 8-64
+    candidates per read, N at 0.1% of genome and read positions."""
+    import torch
+
+    from paper_2103_14978_gb300 import build, device_data as dd, gk, synth
+
+    build.build()
+    stream = torch.cuda.Stream()
+    out = {}
+    for m, e_hi in ((150, 15), (250, 25)):
+        w = synth.config3(m, scale=args.scale)
+        ref = gk.gk_load_reference(w.ref)
+        reads = dd.upload_reads(w.reads, w.read_len, w.stride, stream=stream)
+        pairs = dd.upload_pairs(w.pair_read, w.pair_off, None)
+        acc = torch.empty(w.n_pairs, dtype=torch.uint8, device="cuda")
+        ed = torch.empty(w.n_pairs, dtype=torch.int16, device="cuda")
+        per_e = {}
+        ops = 0
+        for e in range(0, e_hi + 1):
+            f = lambda: gk.gk_filter(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag, m,
+                                     pairs.pair_read, pairs.pair_off, e, accept=acc, edits=ed, stream=stream)
+            for _ in range(args.warmup):
+                f()
+            per_e[e] = time_events(torch, f, max(3, args.steps // 10), stream)
+        torch.cuda.synchronize()
+        undefined = int((dd.edits_u16(ed) == gk.GK_EDITS_UNDEFINED).sum())
+        filtered = w.n_pairs - undefined
+        ops = sum(filtered * ops_per_pair(m, e) for e in per_e)
+        total_ms = sum(per_e.values())
+        out[f"{m}bp"] = {
+            "pairs": w.n_pairs, "undefined_pairs": undefined, "e_sweep": [0, e_hi],
+            "value": w.n_pairs * len(per_e) / (total_ms * 1e-3) / 1e9,
+            "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in per_e.items()},
+            "roofline": {"bound": "alu", "achieved": ops / (total_ms * 1e-3) / 1e12, "peak": ALU_PEAK_TOPS,
+                         "unit": "Tops/s", "frac": ops / (total_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                         "note": "algorithmic ops of the filtered (non-N) pairs"},
+        }
+        ref.close()
+        del reads, pairs, acc, ed
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "filtered pairs/s (x10^9), 150/250 bp, e sweeps, 0.1% N (config 3)",
+                      "unit": "Gpairs/s", "n_gpus": 1, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": "config 3", "scale": args.scale}, "results": out}), flush=True)
+
+
+def run_config4(args):
+    """Config 4: 50M pairs, lengths U{50..300}, per-pair e = ceil(rate m),
+    one persistent graph-captured launch with an autotuned tiling, against the
+    plain filter launched once per read length over the same pairs."""
+    import torch
+
+    from paper_2103_14978_gb300 import batch, build, device_data as dd, gk, synth
+
+    build.build()
+    stream = torch.cuda.current_stream()
+    w = synth.config4(scale=args.scale)
+    ref = gk.gk_load_reference(w.ref)
+    reads = dd.upload_reads(w.reads, w.read_len, w.stride)
+    read_len = dd.as_i16(w.read_len).cuda()
+    pairs = dd.upload_pairs(w.pair_read, w.pair_off, w.pair_e)
+    # autotune on a seeded sample of the pairs
+    rng = np.random.default_rng(3)
+    samp = np.sort(rng.choice(w.n_pairs, min(w.n_pairs, 4_000_000), replace=False))
+    sp = dd.upload_pairs(w.pair_read[samp], w.pair_off[samp], w.pair_e[samp])
+    logs = []
+    best, results = batch.autotune(ref, reads.packed, reads.stride_words, reads.n_reads, read_len, reads.nflag,
+                                   sp.pair_read, sp.pair_off, sp.pair_e, reps=2, budget_s=args.tune_seconds,
+                                   log=logs.append)
+    sig = batch.signature(w.read_len, w.pair_read, w.pair_e)
+    batch.save_table(batch.table_key(sig), best, results)
+    del sp
+    bf = batch.BatchedFilter(ref, reads.packed, reads.stride_words, reads.n_reads, read_len, reads.nflag,
+                             pairs.pair_read, pairs.pair_off, pairs.pair_e, best)
+    bf.capture()
+    for _ in range(args.warmup):
+        bf.replay()
+    steps = max(3, args.steps // 10)
+    batched_ms = time_events(torch, bf.replay, steps, stream)
+    # plain filter: one launch per read length over pairs grouped by length
+    m_pair = w.read_len[w.pair_read]
+    order = np.argsort(m_pair, kind="stable")
+    ms_sorted = m_pair[order]
+    bounds = np.flatnonzero(np.diff(ms_sorted)) + 1
+    starts = np.concatenate([[0], bounds])
+    ends = np.concatenate([bounds, [w.n_pairs]])
+    gp = dd.upload_pairs(w.pair_read[order], w.pair_off[order], w.pair_e[order])
+    acc = torch.empty(w.n_pairs, dtype=torch.uint8, device="cuda")
+    ed = torch.empty(w.n_pairs, dtype=torch.int16, device="cuda")
+
+    def plain():
+        for a, b in zip(starts, ends):
+            gk.gk_filter(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag, int(ms_sorted[a]),
+                         gp.pair_read[a:b], gp.pair_off[a:b], gp.pair_e[a:b], accept=acc[a:b], edits=ed[a:b],
+                         stream=stream)
+
+    for _ in range(args.warmup):
+        plain()
+    plain_ms = time_events(torch, plain, steps, stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(acc.cpu()[torch.from_numpy(np.argsort(order))], bf.accept.cpu()) and
+                torch.equal(ed.cpu()[torch.from_numpy(np.argsort(order))], bf.edits.cpu()))
+    Wp = (m_pair.astype(np.int64) + 31) // 32
+    ek = np.minimum(w.pair_e.astype(np.int64), m_pair.astype(np.int64) - 1)
+    ops = float(np.sum(Wp * (13 + 22 * ek)))
+    line = {
+        "metric": "filtered pairs/s (x10^9), mixed 50-300 bp, per-pair e (config 4)",
+        "value": w.n_pairs / (batched_ms * 1e-3) / 1e9, "unit": "Gpairs/s", "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "config 4: 50M pairs, m U{50..300}, 4 candidates, e=ceil(rate m), shuffled",
+                   "pairs": w.n_pairs, "scale": args.scale, "tiling": list(best), "signature": sig},
+        "plain_per_length": {"value": w.n_pairs / (plain_ms * 1e-3) / 1e9, "ms": plain_ms,
+                             "launches": int(len(starts)), "identical_results": same},
+        "roofline": {"bound": "alu", "achieved": ops / (batched_ms * 1e-3) / 1e12, "peak": ALU_PEAK_TOPS,
+                     "unit": "Tops/s", "frac": ops / (batched_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                     "note": "whole graph (planning + persistent kernel)"},
+        "autotune": {"candidates": {",".join(map(str, k)): v for k, v in results.items()}},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global E_SWEEP
     args = parse_args()
     E_SWEEP = parse_es(args.es)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c3":
+        run_config3(args)
+    elif args.config == "c4":
+        run_config4(args)
     else:
         run_mine(args)
 

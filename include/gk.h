@@ -145,6 +145,46 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
               int count_mode, uint32_t flags, uint8_t *accept_out,
               uint16_t *edits_out, uint32_t *err_count, void *stream);
 
+/* Tiling of the batched filter (chosen by the autotuner). */
+typedef struct {
+  uint32_t words_per_thread; /* words of a pair held per lane: 2, 3, 4, 6 or 8 */
+  uint32_t tile_pairs;       /* pairs per tile (work unit of a warp), 32..65536 */
+  uint32_t blocks_per_sm;    /* persistent grid = SM count x this, 1..32 */
+  uint32_t warps_per_block;  /* 1..32 */
+} gk_tiling_t;
+
+/* Workspace bytes gk_filter_batched needs for n_pairs pairs (6 bytes per
+ * pair plus 80 KiB). */
+uint64_t gk_filter_batched_workspace(uint64_t n_pairs);
+
+/*
+ * gk_filter_batched -- filter pairs of mixed read lengths and per-pair
+ * thresholds in one persistent launch (the paper batches many reads and their
+ * candidates per kernel call, Sec. 3.3 and Sec. 3.5; same per-pair result as
+ * gk_filter, Sec. 2.1/3.3/3.4).
+ *
+ * Arguments as gk_filter, except:
+ *   read_len    device, n_reads uint16 lengths (each read may differ; a read
+ *               longer than GK_MAX_LEN or than 32*stride_words makes its
+ *               pairs invalid)
+ *   tiling      host pointer, see gk_tiling_t
+ *   workspace   device scratch of at least gk_filter_batched_workspace(
+ *               n_pairs) bytes, 256-byte aligned, owned by the caller; its
+ *               contents need no initialisation and are garbage afterwards;
+ *               two calls in flight at once need two workspaces
+ * Enqueues a memset, three planning kernels (classify, scan, scatter) and the
+ * persistent filter kernel on `stream`; everything is stream-ordered and can
+ * be captured in a CUDA graph.  n_pairs must be < 2^32.
+ */
+int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
+                      uint64_t n_reads, const uint16_t *read_len,
+                      const uint8_t *read_nflag, const uint32_t *pair_read,
+                      const uint32_t *pair_off, const uint8_t *pair_e,
+                      uint32_t fixed_e, uint64_t n_pairs, int count_mode,
+                      uint32_t flags, const gk_tiling_t *tiling, void *workspace,
+                      uint64_t workspace_bytes, uint8_t *accept_out,
+                      uint16_t *edits_out, uint32_t *err_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

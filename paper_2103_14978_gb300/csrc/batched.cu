@@ -1,0 +1,199 @@
+// Planning kernels of the batched filter: classify pairs (trivial outcomes
+// written at once, the rest keyed by (W, K)), scan the key histogram into
+// perm slots and tiles (heaviest key first), scatter pair indices by key.
+#include "batched.cuh"
+
+namespace gk {
+
+namespace {
+
+constexpr int kPlanThreads = 256;
+constexpr int kScatterChunk = 2048;  // pairs per scatter block
+
+constexpr int kClassifyChunk = 2048;  // pairs per classify block
+
+// kClassifyChunk pairs per block.  Invalid, undefined (N) and zero-length
+// pairs get their result here (Sec. 3.3 pass-through, the invalid sentinel)
+// and key kNoKey; the others get key (W, K) and are counted in the
+// block-local histogram.
+__global__ void __launch_bounds__(kPlanThreads) classify_kernel(const BatchArgs a) {
+  __shared__ uint32_t hist[kKeys];
+  for (int i = threadIdx.x; i < kKeys; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int it = 0; it < kClassifyChunk / kPlanThreads; ++it) {
+  const uint64_t p = (uint64_t)blockIdx.x * kClassifyChunk + (uint64_t)it * kPlanThreads + threadIdx.x;
+  const bool active = p < a.f.n_pairs;
+  int status = 0;  // 0 filter, 1 undefined, 2 invalid, 3 empty read
+  uint32_t key = kNoKey;
+  if (active) {
+    const uint32_t rid = a.f.pair_read[p];
+    const uint32_t off = a.f.pair_off[p];
+    const uint32_t e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
+    uint32_t m = 0;
+    if ((uint64_t)rid >= a.f.n_reads) {
+      status = 2;
+    } else {
+      m = a.read_len[rid];
+      if (m > GK_MAX_LEN || m > 32u * a.f.stride_words || (uint64_t)off + m > a.f.ref_len) status = 2;
+    }
+    if (status == 0 && m == 0) status = 3;
+    if (status == 0) {
+      if (a.f.read_nflag && a.f.read_nflag[rid]) {
+        status = 1;
+      } else if (a.f.ref_nidx) {
+        const uint2 ni = a.f.ref_nidx[off >> 5];
+        const uint32_t q = ni.x >> (off & 31);
+        const uint64_t firstN = q ? (uint64_t)off + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
+        if (firstN < (uint64_t)off + m) status = 1;
+      }
+    }
+    if (status == 0) {
+      const uint32_t W = (m + 31) / 32;
+      const uint32_t K = min(e, 32u * W);
+      key = key_of(W, min(K, 255u));
+      atomicAdd(&hist[key], 1u);
+    } else {
+      a.f.accept[p] = status != 2;
+      a.f.edits[p] = status == 2 ? GK_EDITS_INVALID : (status == 1 ? GK_EDITS_UNDEFINED : 0);
+    }
+    a.s.key[p] = (uint16_t)key;
+  }
+  if (a.f.err_count) {
+    const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.f.err_count, (unsigned)__popc(bad));
+  }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kKeys; i += blockDim.x)
+    if (hist[i]) atomicAdd(&a.s.hist[i], hist[i]);
+}
+
+// One block: exclusive scans over the key slots in descending key order.
+__global__ void __launch_bounds__(1024) scan_kernel(const BatchArgs a) {
+  constexpr int kPer = kKeys / 1024;  // slots per thread
+  __shared__ uint32_t part_pairs[1024], part_tiles[1024];
+  const int t = threadIdx.x;
+  uint32_t np[kPer], nt[kPer];
+  uint32_t sp = 0, st = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int slot = t * kPer + j;
+    np[j] = a.s.hist[kKeys - 1 - slot];
+    nt[j] = (np[j] + a.tile_pairs - 1) / a.tile_pairs;
+    sp += np[j];
+    st += nt[j];
+  }
+  part_pairs[t] = sp;
+  part_tiles[t] = st;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
+    uint32_t vp = 0, vt = 0;
+    if (t >= off) {
+      vp = part_pairs[t - off];
+      vt = part_tiles[t - off];
+    }
+    __syncthreads();
+    part_pairs[t] += vp;
+    part_tiles[t] += vt;
+    __syncthreads();
+  }
+  uint32_t bp = part_pairs[t] - sp, bt = part_tiles[t] - st;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int slot = t * kPer + j;
+    a.s.pair_base[slot] = bp;
+    a.s.tile_base[slot] = bt;
+    a.s.cursor[kKeys - 1 - slot] = bp;
+    bp += np[j];
+    bt += nt[j];
+  }
+  if (t == 1023) {
+    a.s.pair_base[kKeys] = bp;
+    a.s.tile_base[kKeys] = bt;
+    a.s.counters[0] = 0;
+    a.s.counters[1] = bt;
+  }
+}
+
+// Each block takes kScatterChunk pairs: a block histogram reserves one range
+// per key in the global cursors, then every pair takes a slot in its range.
+__global__ void __launch_bounds__(kPlanThreads) scatter_kernel(const BatchArgs a) {
+  __shared__ uint32_t local[kKeys];
+  for (int i = threadIdx.x; i < kKeys; i += blockDim.x) local[i] = 0;
+  __syncthreads();
+  const uint64_t p0 = (uint64_t)blockIdx.x * kScatterChunk;
+  const uint64_t p1 = min_u64(p0 + kScatterChunk, a.f.n_pairs);
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const uint16_t k = a.s.key[p];
+    if (k != kNoKey) atomicAdd(&local[k], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kKeys; i += blockDim.x)
+    if (local[i]) local[i] = atomicAdd(&a.s.cursor[i], local[i]);
+  __syncthreads();
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const uint16_t k = a.s.key[p];
+    if (k != kNoKey) a.s.perm[atomicAdd(&local[k], 1u)] = (uint32_t)p;
+  }
+}
+
+}  // namespace
+
+uint64_t batch_scratch_bytes(uint64_t n_pairs) {
+  auto up = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+  return up(2 * n_pairs) + up(4 * n_pairs) + 2 * up(4 * kKeys) + 2 * up(4 * (kKeys + 1)) + up(16);
+}
+
+BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs) {
+  auto up = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+  char *b = static_cast<char *>(base);
+  BatchScratch s;
+  s.key = reinterpret_cast<uint16_t *>(b);
+  b += up(2 * n_pairs);
+  s.perm = reinterpret_cast<uint32_t *>(b);
+  b += up(4 * n_pairs);
+  s.hist = reinterpret_cast<uint32_t *>(b);
+  b += up(4 * kKeys);
+  s.cursor = reinterpret_cast<uint32_t *>(b);
+  b += up(4 * kKeys);
+  s.pair_base = reinterpret_cast<uint32_t *>(b);
+  b += up(4 * (kKeys + 1));
+  s.tile_base = reinterpret_cast<uint32_t *>(b);
+  b += up(4 * (kKeys + 1));
+  s.counters = reinterpret_cast<uint32_t *>(b);
+  return s;
+}
+
+cudaError_t launch_persistent_wpt2(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_persistent_wpt3(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_persistent_wpt4(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_persistent_wpt6(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_persistent_wpt8(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+
+cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, uint32_t warps_per_block,
+                           cudaStream_t stream) {
+  if (a.f.n_pairs == 0) return cudaSuccess;
+  cudaError_t err = cudaMemsetAsync(a.s.hist, 0, sizeof(uint32_t) * kKeys, stream);
+  if (err != cudaSuccess) return err;
+  const unsigned cblocks = (unsigned)((a.f.n_pairs + kClassifyChunk - 1) / kClassifyChunk);
+  classify_kernel<<<cblocks, kPlanThreads, 0, stream>>>(a);
+  scan_kernel<<<1, 1024, 0, stream>>>(a);
+  const unsigned sblocks = (unsigned)((a.f.n_pairs + kScatterChunk - 1) / kScatterChunk);
+  scatter_kernel<<<sblocks, kPlanThreads, 0, stream>>>(a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t grid = (uint32_t)sms * blocks_per_sm;
+  switch (wpt) {
+    case 2: return launch_persistent_wpt2(a, grid, warps_per_block, stream);
+    case 3: return launch_persistent_wpt3(a, grid, warps_per_block, stream);
+    case 4: return launch_persistent_wpt4(a, grid, warps_per_block, stream);
+    case 6: return launch_persistent_wpt6(a, grid, warps_per_block, stream);
+    case 8: return launch_persistent_wpt8(a, grid, warps_per_block, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gk

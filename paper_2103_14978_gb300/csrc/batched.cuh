@@ -1,0 +1,118 @@
+// Batched filter over pairs of mixed read lengths and per-pair thresholds
+// (the paper batches many reads and candidates per launch, Sec. 3.3/3.5; here
+// one persistent launch covers every length).
+//
+// Work is grouped by key = (W, K): W = ceil(m/32) words per read, K =
+// min(e, 32W) shift steps.  A tile is up to tile_pairs pairs of one key, so a
+// warp's control flow is uniform; persistent warps take tiles from one
+// atomic counter, heaviest keys first.
+#pragma once
+
+#include "coop.cuh"
+#include "gk_internal.cuh"
+
+namespace gk {
+
+constexpr int kKeys = 16 * 256;  // W in 1..16, K in 0..255
+constexpr uint16_t kNoKey = 0xFFFF;
+
+__host__ __device__ __forceinline__ uint32_t key_of(uint32_t W, uint32_t K) { return (W - 1) * 256 + K; }
+__host__ __device__ __forceinline__ uint32_t key_W(uint32_t key) { return key / 256 + 1; }
+__host__ __device__ __forceinline__ uint32_t key_K(uint32_t key) { return key % 256; }
+
+// Scratch of the batched path (all device memory, caller-provided).
+struct BatchScratch {
+  uint16_t *key;        // n_pairs
+  uint32_t *perm;       // n_pairs: pair indices grouped by key
+  uint32_t *hist;       // kKeys pair counts
+  uint32_t *cursor;     // kKeys scatter cursors
+  uint32_t *pair_base;  // kKeys + 1: first perm slot of each key (descending key order)
+  uint32_t *tile_base;  // kKeys + 1: first tile of each key (descending key order)
+  uint32_t *counters;   // [0] next tile, [1] tile count
+};
+
+struct BatchArgs {
+  FilterArgs f;               // shared fields; f.m is unused (per-read lengths)
+  const uint16_t *read_len;   // n_reads lengths
+  uint32_t tile_pairs;
+  BatchScratch s;
+};
+
+// Byte size of the scratch for n_pairs pairs and the layout inside one
+// 256-aligned workspace.
+uint64_t batch_scratch_bytes(uint64_t n_pairs);
+BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs);
+
+cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, uint32_t warps_per_block,
+                           cudaStream_t stream);
+
+template <int WPT>
+cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
+
+// Persistent filter body, shared by every WPT instantiation.
+template <int WPT>
+__global__ void persistent_kernel(const BatchArgs a) {
+  const int lane = threadIdx.x & 31;
+  const bool edge_on = a.f.edge_on != 0;
+  const uint32_t n_tiles = a.s.counters[1];
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&a.s.counters[0], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_tiles) break;
+    // Key of tile t: the last key slot (descending order) whose tile_base <= t.
+    int lo = 0, hi = kKeys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.s.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t key = (uint32_t)(kKeys - 1 - lo);  // slot 0 is the heaviest key
+    const uint32_t W = key_W(key), K = key_K(key);
+    const uint32_t first = a.s.pair_base[lo] + (t - a.s.tile_base[lo]) * a.tile_pairs;
+    const uint32_t end = min(first + a.tile_pairs, a.s.pair_base[lo + 1]);
+    Group g;
+    g.L = (int)((W + WPT - 1) / WPT);
+    const int ppw = 32 / g.L;
+    const int grp = lane / g.L;
+    g.lig = lane - grp * g.L;
+    for (uint32_t base = first; base < end; base += (uint32_t)ppw) {
+      const uint32_t slot = base + (uint32_t)grp;
+      const bool valid = grp < ppw && slot < end;
+      uint32_t rh[WPT], rl[WPT], gh[WPT], gl[WPT], vm[WPT];
+      uint32_t p = 0, e = 0, m = 0;
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) rh[j] = rl[j] = gh[j] = gl[j] = vm[j] = 0;
+      if (valid) {
+        p = a.s.perm[slot];
+        const uint32_t rid = a.f.pair_read[p];
+        const uint32_t off = a.f.pair_off[p];
+        e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
+        m = a.read_len[rid];
+        const uint2 *rp = a.f.reads + (uint64_t)rid * a.f.stride_words;
+        const uint2 *gp = a.f.ref_hl + (off >> 5);
+        const uint32_t sh = off & 31;
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+          const uint32_t w = (uint32_t)(g.lig * WPT + j);
+          if (w < W) {
+            const int64_t rem = (int64_t)m - 32 * (int64_t)w;
+            vm[j] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+            const uint2 r = rp[w];
+            rh[j] = r.x & vm[j];
+            rl[j] = r.y & vm[j];
+            const uint2 c0 = gp[w], c1 = gp[w + 1];
+            gh[j] = __funnelshift_r(c0.x, c1.x, sh) & vm[j];
+            gl[j] = __funnelshift_r(c0.y, c1.y, sh) & vm[j];
+          }
+        }
+      }
+      const uint32_t count = coop_filter<WPT>(rh, rl, gh, gl, vm, K, edge_on, a.f.count_mode, g);
+      if (valid && g.lig == 0) {
+        a.f.accept[p] = count <= e;
+        a.f.edits[p] = (uint16_t)count;
+      }
+    }
+  }
+}
+
+}  // namespace gk

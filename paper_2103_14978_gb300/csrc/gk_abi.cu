@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "batched.cuh"
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -235,6 +236,63 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.edits = edits_out;
   a.err_count = err_count;
   return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
+}
+
+uint64_t gk_filter_batched_workspace(uint64_t n_pairs) { return gk::batch_scratch_bytes(n_pairs); }
+
+int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64_t n_reads,
+                      const uint16_t *read_len, const uint8_t *read_nflag, const uint32_t *pair_read,
+                      const uint32_t *pair_off, const uint8_t *pair_e, uint32_t fixed_e, uint64_t n_pairs,
+                      int count_mode, uint32_t flags, const gk_tiling_t *tiling, void *workspace,
+                      uint64_t workspace_bytes, uint8_t *accept_out, uint16_t *edits_out,
+                      uint32_t *err_count, void *stream) {
+  gk::clear_error();
+  if (!ref) return fail(GK_EINVAL, "gk_filter_batched: null reference handle");
+  if (n_pairs == 0) return GK_OK;
+  if (n_pairs >= (1ull << 32)) return fail(GK_ERANGE, "gk_filter_batched: n_pairs must be < 2^32");
+  if (!reads || !read_len || !pair_read || !pair_off || !accept_out || !edits_out || !tiling)
+    return fail(GK_EINVAL, "gk_filter_batched: null buffer");
+  if (stride_words == 0 || stride_words > GK_MAX_LEN / 32)
+    return fail(GK_EINVAL, "gk_filter_batched: stride_words must be 1..GK_MAX_LEN/32");
+  if (!aligned(reads, 8)) return fail(GK_EINVAL, "gk_filter_batched: reads must be 8-byte aligned");
+  if (!pair_e && fixed_e > 255) return fail(GK_ERANGE, "gk_filter_batched: fixed_e above 255");
+  if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
+    return fail(GK_EINVAL, "gk_filter_batched: unknown count_mode");
+  if (flags & ~GK_FLAG_NO_EDGE_FIX) return fail(GK_EINVAL, "gk_filter_batched: unknown flags");
+  const gk_tiling_t t = *tiling;
+  if (!(t.words_per_thread == 2 || t.words_per_thread == 3 || t.words_per_thread == 4 ||
+        t.words_per_thread == 6 || t.words_per_thread == 8))
+    return fail(GK_EINVAL, "gk_filter_batched: words_per_thread must be 2, 3, 4, 6 or 8");
+  if (t.tile_pairs < 32 || t.tile_pairs > 65536 || t.blocks_per_sm < 1 || t.blocks_per_sm > 32 ||
+      t.warps_per_block < 1 || t.warps_per_block > 32)
+    return fail(GK_EINVAL, "gk_filter_batched: tiling out of range");
+  if (!workspace || !aligned(workspace, 256) || workspace_bytes < gk::batch_scratch_bytes(n_pairs))
+    return fail(GK_EINVAL, "gk_filter_batched: workspace missing, unaligned or too small");
+  gk::BatchArgs a{};
+  a.f.ref_hl = ref->hl;
+  a.f.ref_nidx = ref->nidx;
+  a.f.ref_len = ref->n_bases;
+  a.f.reads = reinterpret_cast<const uint2 *>(reads);
+  a.f.stride_words = stride_words;
+  a.f.n_reads = n_reads;
+  a.f.read_nflag = read_nflag;
+  a.f.m = 0;
+  a.f.pair_read = pair_read;
+  a.f.pair_off = pair_off;
+  a.f.pair_e = pair_e;
+  a.f.fixed_e = fixed_e;
+  a.f.n_pairs = n_pairs;
+  a.f.count_mode = count_mode;
+  a.f.edge_on = (flags & GK_FLAG_NO_EDGE_FIX) ? 0 : 1;
+  a.f.accept = accept_out;
+  a.f.edits = edits_out;
+  a.f.err_count = err_count;
+  a.read_len = read_len;
+  a.tile_pairs = t.tile_pairs;
+  a.s = gk::batch_scratch_layout(workspace, n_pairs);
+  return gk::cuda_check(gk::launch_batched((int)t.words_per_thread, a, t.blocks_per_sm, t.warps_per_block,
+                                           (cudaStream_t)stream),
+                        "gk_filter_batched: launch");
 }
 
 }  // extern "C"

@@ -39,7 +39,24 @@ _SIGS = {
                    _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
                    _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_probe_alu": ([_c.c_int, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_batched_workspace": ([_c.c_uint64], _c.c_uint64),
+    "gk_filter_batched": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_void_p,
+                           _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
+                           _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p,
+                           _c.c_void_p, _c.c_void_p], _c.c_int),
 }
+
+
+class Tiling(ctypes.Structure):
+    """gk_tiling_t: words per lane, pairs per tile, persistent grid shape."""
+    _fields_ = [("words_per_thread", ctypes.c_uint32), ("tile_pairs", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32)]
+
+    def astuple(self):
+        return (self.words_per_thread, self.tile_pairs, self.blocks_per_sm, self.warps_per_block)
+
+    def __repr__(self):
+        return "Tiling(wpt=%d, tile=%d, blocks/SM=%d, warps/block=%d)" % self.astuple()
 
 
 class GKError(RuntimeError):
@@ -203,6 +220,38 @@ def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: i
         pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
         _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1),
         _stream(stream)))
+    return accept, edits
+
+
+def gk_filter_batched_workspace(n_pairs: int) -> int:
+    return int(lib().gk_filter_batched_workspace(n_pairs))
+
+
+def gk_filter_batched(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: int,
+                      read_len: torch.Tensor, read_nflag: torch.Tensor | None, pair_read: torch.Tensor,
+                      pair_off: torch.Tensor, e, tiling: Tiling, workspace: torch.Tensor,
+                      count_mode: int = GK_COUNT_RUNS4, flags: int = 0, accept: torch.Tensor | None = None,
+                      edits: torch.Tensor | None = None, err_count: torch.Tensor | None = None, stream=None):
+    """Filter pairs of mixed read lengths in one persistent launch
+    (gk_filter_batched).  ``read_len`` is an int16 CUDA tensor (uint16
+    values); ``workspace`` a uint8 CUDA tensor of at least
+    gk_filter_batched_workspace(n) bytes.  Returns (accept, edits)."""
+    n = pair_read.numel()
+    dev = pair_read.device
+    if accept is None:
+        accept = torch.empty(n, dtype=torch.uint8, device=dev)
+    if edits is None:
+        edits = torch.empty(n, dtype=torch.int16, device=dev)
+    if reads.numel() < n_reads * stride_words * 2:
+        raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
+    pe, fixed_e = (_dptr(e, torch.uint8, "e", n), 0) if isinstance(e, torch.Tensor) else (None, int(e))
+    _check(lib().gk_filter_batched(
+        ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
+        _dptr(read_len, torch.int16, "read_len", n_reads), _dptr(read_nflag, torch.uint8, "read_nflag", n_reads),
+        _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n), pe, fixed_e, n,
+        count_mode, flags, ctypes.byref(tiling), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
+        _dptr(accept, torch.uint8, "accept", n), _dptr(edits, torch.int16, "edits", n),
+        _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
     return accept, edits
 
 

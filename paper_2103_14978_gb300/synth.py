@@ -220,7 +220,7 @@ def pairs_workload(name: str, *, seed: int, ref: np.ndarray, n_pairs: int, m, ca
     if e is None:
         rates = np.asarray(e_rates, dtype=np.float64)
         r = rates[rng.integers(0, rates.shape[0], n_pairs)]
-        pair_e = np.ceil(np.round(r * m_pair, 9)).astype(np.uint8)
+        pair_e = np.minimum(np.ceil(np.round(r * m_pair, 9)), 255).astype(np.uint8)
     if shuffle:
         perm = rng.permutation(n_pairs)
         pair_read, pair_off = pair_read[perm], pair_off[perm]
