@@ -185,6 +185,39 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
                       uint64_t workspace_bytes, uint8_t *accept_out,
                       uint16_t *edits_out, uint32_t *err_count, void *stream);
 
+/*
+ * gk_filter_batched_noalloc -- gk_filter_batched for callers that cannot
+ * allocate device memory when they filter: for example a plugin inside a host
+ * application whose device memory is all owned by the application's own
+ * pool, or a latency-bound thread that must not call cudaMalloc because it can
+ * synchronise the whole device.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *
+ * Same arguments and results as gk_filter_batched, without the workspace:
+ * the scratch is a fixed array inside the library image (about 5.8 MiB per
+ * GPU, held by every GPU that loads the library until the process exits).
+ * The call allocates nothing.
+ *   - n_pairs is limited to GK_NOALLOC_MAX_PAIRS; larger batches return
+ *     GK_ERANGE with a message (use gk_filter_batched then).
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array and each call overwrites it.  Calls whose
+ *     work overlaps on the GPU (e.g. on two streams without ordering) race
+ *     and give wrong results: keep them ordered on one stream or serialise
+ *     them.
+ */
+#define GK_NOALLOC_MAX_PAIRS 1000000u
+
+int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
+                              uint32_t stride_words, uint64_t n_reads,
+                              const uint16_t *read_len, const uint8_t *read_nflag,
+                              const uint32_t *pair_read, const uint32_t *pair_off,
+                              const uint8_t *pair_e, uint32_t fixed_e,
+                              uint64_t n_pairs, int count_mode, uint32_t flags,
+                              const gk_tiling_t *tiling, uint8_t *accept_out,
+                              uint16_t *edits_out, uint32_t *err_count,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

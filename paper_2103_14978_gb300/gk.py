@@ -44,7 +44,13 @@ _SIGS = {
                            _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
                            _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p,
                            _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_batched_noalloc": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p,
+                                   _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32,
+                                   _c.c_uint64, _c.c_int, _c.c_uint32, _c.c_void_p, _c.c_void_p,
+                                   _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
 }
+
+GK_NOALLOC_MAX_PAIRS = 1_000_000
 
 
 class Tiling(ctypes.Structure):
@@ -252,6 +258,28 @@ def gk_filter_batched(ref: Reference, reads: torch.Tensor, stride_words: int, n_
         count_mode, flags, ctypes.byref(tiling), _dptr(workspace, torch.uint8, "workspace"), workspace.numel(),
         _dptr(accept, torch.uint8, "accept", n), _dptr(edits, torch.int16, "edits", n),
         _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    return accept, edits
+
+
+def gk_filter_batched_noalloc(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: int,
+                              read_len: torch.Tensor, read_nflag: torch.Tensor | None, pair_read: torch.Tensor,
+                              pair_off: torch.Tensor, e, tiling: Tiling, accept: torch.Tensor,
+                              edits: torch.Tensor, count_mode: int = GK_COUNT_RUNS4, flags: int = 0,
+                              err_count: torch.Tensor | None = None, stream=None):
+    """gk_filter_batched without a workspace, for callers that must not
+    allocate device memory while filtering: the library keeps a fixed scratch
+    array of its own (at most GK_NOALLOC_MAX_PAIRS pairs per call; calls that
+    overlap on the GPU race on it).  The caller provides the outputs."""
+    n = pair_read.numel()
+    if reads.numel() < n_reads * stride_words * 2:
+        raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
+    pe, fixed_e = (_dptr(e, torch.uint8, "e", n), 0) if isinstance(e, torch.Tensor) else (None, int(e))
+    _check(lib().gk_filter_batched_noalloc(
+        ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
+        _dptr(read_len, torch.int16, "read_len", n_reads), _dptr(read_nflag, torch.uint8, "read_nflag", n_reads),
+        _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n), pe, fixed_e, n,
+        count_mode, flags, ctypes.byref(tiling), _dptr(accept, torch.uint8, "accept", n),
+        _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
     return accept, edits
 
 
