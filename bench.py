@@ -60,7 +60,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--es", default="0-10", help="thresholds of the sweep, e.g. 0-10 or 2,10")
     ap.add_argument("--probe-all", action="store_true", help="run every integer probe kind")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--requests", type=int, default=4000, help="requests per load level (config 5)")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: the default line; c3: 150/250 bp with N; c4: batched mixed lengths")
     ap.add_argument("--tune-seconds", type=float, default=60.0, help="autotuner budget (config 4)")
     return ap.parse_args()
@@ -590,6 +591,67 @@ def run_config4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_config5(args):
+    """Config 5: serving.  Resident 100 Mbp genome; Poisson arrivals of
+    requests of log-uniform 1k-1M pairs, m in {100, 150, 250}, one
+    e = ceil(rate m) per request; offered load 0.5 / 0.8 / 0.95 of the plain
+    filter's measured capacity on the same mix."""
+    import torch
+
+    from paper_2103_14978_gb300 import build, gk, serve, synth
+
+    build.build()
+    ref = synth.reference()
+    gkref = gk.gk_load_reference(ref)
+    lengths, rates = (100, 150, 250), (0.02, 0.05, 0.10)
+    pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000)
+    # plain-filter capacity on the mix: every (m, e) pair equally likely
+    stream = torch.cuda.current_stream()
+    per_combo = {}
+    for m in lengths:
+        p = pool.by_len[m]
+        n = p["pair_read"][1].shape[0]
+        packed = p["packed"][0].cuda()
+        nflag = p["nflag"][0].cuda()
+        pr = p["pair_read"][0].cuda()
+        po = p["pair_off"][0].cuda()
+        acc = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ed = torch.empty(n, dtype=torch.int16, device="cuda")
+        for rate in rates:
+            e = int(np.ceil(round(rate * m, 9)))
+            f = lambda: gk.gk_filter(gkref, packed, pool.sw, p["lens"][1].shape[0], nflag, m, pr, po, e,
+                                     accept=acc, edits=ed)
+            f()
+            per_combo[f"{m}bp_e{e}"] = n / (time_events(torch, f, 5, stream) * 1e-3)
+    capacity = 1.0 / np.mean([1.0 / v for v in per_combo.values()])
+    lo, hi = 1_000, 1_000_000
+    mean_size = (hi - lo) / np.log(hi / lo)
+    cfg = serve.ServeConfig(mem_cap_bytes=8 << 30, max_round_pairs=8_000_000, copy_results=False)
+    ex = serve.GpuExecutor(gkref, cfg)
+    levels = {}
+    for load in (0.5, 0.8, 0.95):
+        plan = serve.poisson_plan(args.requests, load * capacity / mean_size, 2103_14978 + 5 + int(load * 100))
+        reqs = [pool.request(q["id"], q["m"], q["e"], q["n_pairs"], q["start"], q["arrival"]) for q in plan]
+        srv = serve.Server(ex, cfg)
+        t0 = time.perf_counter()
+        srv.run(reqs)
+        wall = time.perf_counter() - t0
+        summ = serve.latency_summary(reqs)
+        summ.update({"offered_gpairs_s": load * capacity / 1e9, "rounds": srv.rounds_launched,
+                     "mean_requests_per_round": float(np.mean(srv.coalesced)), "wall_s": wall,
+                     "requests": len(reqs), "max_inflight_rounds": srv.max_inflight_seen})
+        levels[str(load)] = summ
+    line = {"metric": "serving: p50/p99 latency and pairs/s (config 5)", "unit": "Gpairs/s", "n_gpus": 1,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "config 5: Poisson requests of 1k-1M pairs, m in {100,150,250}, "
+                                   "e = ceil(rate m), rate in {2,5,10}%", "requests_per_level": args.requests,
+                       "ring_read_slots": ex.n_read_slots, "ring_pair_slots": ex.n_pair_slots},
+            "plain_capacity_gpairs_s": capacity / 1e9,
+            "plain_per_combo_gpairs_s": {k: v / 1e9 for k, v in per_combo.items()},
+            "levels": levels}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global E_SWEEP
     args = parse_args()
@@ -600,6 +662,8 @@ def main():
         run_config3(args)
     elif args.config == "c4":
         run_config4(args)
+    elif args.config == "c5":
+        run_config5(args)
     else:
         run_mine(args)
 

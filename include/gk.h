@@ -186,6 +186,37 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
                       uint16_t *edits_out, uint32_t *err_count, void *stream);
 
 /*
+ * gk_rebase_pairs -- read-id rebasing for coalesced launches.  When the pairs
+ * of several requests are concatenated into one launch (continuous batching;
+ * the paper fills one batch with many reads and their candidates, Sec. 3.5),
+ * each request's read ids are relative to its own reads; this adds a
+ * per-request offset in place and, optionally, writes each request's
+ * threshold into every one of its pairs.
+ *
+ *   pair_read  device, n_pairs uint32, rewritten in place
+ *   pair_e     device, n_pairs uint8 written from seg_e, or NULL
+ *   seg_end    device, n_segs uint64: cumulative pair counts (request i owns
+ *              pairs [seg_end[i-1], seg_end[i]), the last value >= n_pairs)
+ *   seg_delta  device, n_segs int64: offset added to request i's read ids
+ *   seg_e      device, n_segs uint8 thresholds (needed when pair_e is set)
+ * A result outside 0..2^32-1 becomes 0xFFFFFFFF, which the filters report as
+ * an invalid pair.  Asynchronous on `stream`.
+ */
+int gk_rebase_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs,
+                    const uint64_t *seg_end, const int64_t *seg_delta,
+                    const uint8_t *seg_e, uint32_t n_segs, void *stream);
+
+/*
+ * gk_copy_many -- n asynchronous copies on `stream`, one cudaMemcpyAsync
+ * each (kind 1: host to device, 2: device to host, 3: device to device), so
+ * that a coalesced launch moves many requests' inputs with one call.  Host
+ * buffers should be pinned for the copies to be asynchronous.  Stops at the
+ * first failing copy with GK_ECUDA.
+ */
+int gk_copy_many(void *const *dst, const void *const *src, const uint64_t *bytes,
+                 uint32_t n, int kind, void *stream);
+
+/*
  * gk_filter_batched_noalloc -- gk_filter_batched for callers that cannot
  * allocate device memory when they filter: for example a plugin inside a host
  * application whose device memory is all owned by the application's own

@@ -48,6 +48,9 @@ _SIGS = {
                                    _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32,
                                    _c.c_uint64, _c.c_int, _c.c_uint32, _c.c_void_p, _c.c_void_p,
                                    _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_rebase_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                         _c.c_uint32, _c.c_void_p], _c.c_int),
+    "gk_copy_many": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_int, _c.c_void_p], _c.c_int),
 }
 
 GK_NOALLOC_MAX_PAIRS = 1_000_000
@@ -281,6 +284,31 @@ def gk_filter_batched_noalloc(ref: Reference, reads: torch.Tensor, stride_words:
         count_mode, flags, ctypes.byref(tiling), _dptr(accept, torch.uint8, "accept", n),
         _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
     return accept, edits
+
+
+def gk_rebase_pairs(pair_read: torch.Tensor, seg_end: torch.Tensor, seg_delta: torch.Tensor,
+                    pair_e: torch.Tensor | None = None, seg_e: torch.Tensor | None = None, stream=None):
+    """Add request i's offset seg_delta[i] to the read ids of its pairs
+    [seg_end[i-1], seg_end[i]) in place and, if ``pair_e`` is given, write its
+    threshold seg_e[i] into them (gk_rebase_pairs)."""
+    n_segs = seg_end.numel()
+    n = pair_read.numel()
+    _check(lib().gk_rebase_pairs(_dptr(pair_read, torch.int32, "pair_read"),
+                                 _dptr(pair_e, torch.uint8, "pair_e", n), n,
+                                 _dptr(seg_end, torch.int64, "seg_end"), _dptr(seg_delta, torch.int64, "seg_delta", n_segs),
+                                 _dptr(seg_e, torch.uint8, "seg_e", n_segs), n_segs, _stream(stream)))
+
+
+H2D, D2H, D2D = 1, 2, 3
+
+
+def gk_copy_many(dst: np.ndarray, src: np.ndarray, nbytes: np.ndarray, kind: int, stream=None):
+    """Enqueue len(dst) copies (uint64 address arrays) with one call."""
+    dst = np.ascontiguousarray(dst, np.uint64)
+    src = np.ascontiguousarray(src, np.uint64)
+    nbytes = np.ascontiguousarray(nbytes, np.uint64)
+    _check(lib().gk_copy_many(dst.ctypes.data, src.ctypes.data, nbytes.ctypes.data, dst.shape[0], kind,
+                              _stream(stream)))
 
 
 GK_PROBE_LOP3, GK_PROBE_SHF, GK_PROBE_MIX = 0, 1, 2

@@ -1,0 +1,479 @@
+"""Continuous-batching server for the filter: the encoded genome stays
+resident, requests (reads + candidate pairs + one threshold) are admitted as
+device memory frees up, coalesced into shared launches, and their work
+overlaps on two streams.
+
+Memory admission.  At start the server sizes two device rings from the free
+device memory (or a cap): read slots (ASCII row, packed planes, length, N
+flag) and pair slots (read id, offset, threshold, accept, edits).  A request
+is admitted when both rings have room for it, in arrival order; its slots are
+released when its launch has completed.  A request larger than the rings is
+rejected.
+
+Requests arrive host-encoded (2-bit planes written by gk_encode's host path,
+the paper's host-encoded mode, Sec. 3.3): a 100 bp read moves as 32 bytes
+instead of 100.
+
+Rounds.  Whenever a stream is free, every admitted request not yet launched
+(up to `max_round_pairs` pairs) forms one round: one gk_copy_many call moves
+all their inputs host to device (one copy per array per request), one
+gk_rebase_pairs moves each request's read ids to its slots and writes its
+threshold into its pairs, one gk_filter_batched filters every pair (any mix
+of read lengths and thresholds), and one gk_copy_many copies the results back
+to pinned host memory.  Two events per round give the device-side and
+host-side completion times.
+
+The filter work is entirely in libgk; this module is the scheduler.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+GK_MAX_WORDS = 16
+
+
+@dataclasses.dataclass
+class Request:
+    """One request: ``packed`` uint32 reads as gk_encode writes them
+    (n_reads x stride_words x 2, the server's stride), ``nflag`` uint8 and
+    ``lens`` uint16 per read, ``pair_read`` uint32 ids relative to these
+    reads, ``pair_off`` uint32 genome offsets, one threshold ``e``.  For
+    asynchronous copies the arrays should live in pinned host memory.
+    ``arrival`` is the time (s, from the start of ``run``) the request arrives."""
+
+    id: int
+    packed: np.ndarray
+    nflag: np.ndarray
+    lens: np.ndarray
+    pair_read: np.ndarray
+    pair_off: np.ndarray
+    e: int
+    arrival: float = 0.0
+    max_len: int = -1  # longest read, if known (else computed from lens)
+    status: str = "queued"  # queued, admitted, running, done, rejected, cancelled, failed
+    error: str = ""
+    read_slot: int = -1
+    pair_slot: int = -1
+    t_admit: float = float("nan")
+    t_dispatch: float = float("nan")
+    t_device_done: float = float("nan")
+    t_done: float = float("nan")
+    accept: np.ndarray | None = None
+    edits: np.ndarray | None = None
+    ascii: np.ndarray | None = None  # the reads' ASCII rows, kept only for checking
+
+    @property
+    def n_reads(self) -> int:
+        return int(self.lens.shape[0])
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.pair_read.shape[0])
+
+    def cancel(self) -> bool:
+        """Cancel a request that has not been admitted yet."""
+        if self.status == "queued":
+            self.status = "cancelled"
+            return True
+        return False
+
+
+def encode_request(rid: int, reads_ascii: np.ndarray, lens: np.ndarray, pair_read: np.ndarray,
+                   pair_off: np.ndarray, e: int, stride_words: int = 8, arrival: float = 0.0) -> Request:
+    """Build a request from ASCII reads (n_reads x row bytes) with the
+    library's host encoder."""
+    import torch
+
+    from . import gk
+
+    n = int(lens.shape[0])
+    rows = np.ascontiguousarray(reads_ascii, np.uint8).reshape(n, -1)
+    packed, nflag = gk.gk_encode(torch.from_numpy(rows.reshape(-1)), n, rows.shape[1],
+                                 lens=torch.from_numpy(np.ascontiguousarray(lens, np.uint16).view(np.int16)),
+                                 stride_words=stride_words)
+    return Request(rid, packed.numpy().view(np.uint32), nflag.numpy(), np.ascontiguousarray(lens, np.uint16),
+                   np.ascontiguousarray(pair_read, np.uint32), np.ascontiguousarray(pair_off, np.uint32), int(e),
+                   arrival=arrival, max_len=int(lens.max(initial=0)))
+
+
+class FifoRing:
+    """Contiguous slot ranges handed out and released in FIFO order from a
+    circular buffer of `size` slots (an allocation never wraps; the tail gap
+    it skips is free again once the older allocations are released)."""
+
+    def __init__(self, size: int):
+        self.size = int(size)
+        self.live = collections.deque()  # (start, n) in allocation order
+        self.head = 0
+
+    def free_slots(self) -> int:
+        return self.size - sum(n for _, n in self.live)
+
+    def alloc(self, n: int):
+        n = int(n)
+        if n <= 0 or n > self.size:
+            raise ValueError(f"allocation of {n} slots in a ring of {self.size}")
+        if not self.live:
+            self.head = 0
+            start = 0
+        else:
+            tail = self.live[0][0]
+            if self.head > tail:
+                if self.head + n <= self.size:
+                    start = self.head
+                elif n <= tail:
+                    start = 0
+                else:
+                    return None
+            elif self.head < tail:
+                if self.head + n <= tail:
+                    start = self.head
+                else:
+                    return None
+            else:  # head == tail with live allocations: full
+                return None
+        self.live.append((start, n))
+        self.head = start + n
+        return start
+
+    def undo_last(self):
+        start, _ = self.live.pop()
+        self.head = start if self.live else 0
+
+    def release_oldest(self):
+        self.live.popleft()
+        if not self.live:
+            self.head = 0
+
+
+@dataclasses.dataclass
+class ServeConfig:
+    stride_words: int = 8             # packed words per read (reads up to 32 x this)
+    max_read_len: int = 256
+    pairs_per_read: float = 4.0       # expected candidates per read, to split the memory budget
+    mem_fraction: float = 0.25        # share of the free device memory the rings may take
+    mem_cap_bytes: int | None = None  # hard cap on the rings' memory (simulated small device)
+    max_round_pairs: int = 4_000_000
+    n_streams: int = 2
+    tiling: tuple = (4, 256, 4, 8)
+    round_timeout_s: float = 30.0     # host watchdog on a launched round
+    copy_results: bool = True         # copy each request's results out of the result ring
+
+
+@dataclasses.dataclass
+class Round:
+    requests: list
+    slot: int
+    handle: object = None
+    t_dispatch: float = 0.0
+
+
+class Server:
+    """Scheduler over an executor (GpuExecutor on a GPU, a fake in host-logic
+    tests)."""
+
+    def __init__(self, executor, config: ServeConfig):
+        self.ex = executor
+        self.cfg = config
+        self.read_ring = FifoRing(executor.n_read_slots)
+        self.pair_ring = FifoRing(executor.n_pair_slots)
+        self.rounds_launched = 0
+        self.max_inflight_seen = 0
+        self.coalesced = []  # requests per round
+
+    def fits_at_all(self, r: Request) -> bool:
+        return (r.n_reads <= self.read_ring.size and r.n_pairs <= self.pair_ring.size
+                and r.n_pairs <= self.cfg.max_round_pairs
+                and (r.max_len if r.max_len >= 0 else int(r.lens.max(initial=0))) <= self.cfg.max_read_len
+                and r.packed.size == r.n_reads * self.cfg.stride_words * 2 and 0 <= r.e <= 255)
+
+    def _admit(self, r: Request, now: float) -> bool:
+        rs = self.read_ring.alloc(r.n_reads)
+        if rs is None:
+            return False
+        ps = self.pair_ring.alloc(r.n_pairs)
+        if ps is None:
+            self.read_ring.undo_last()
+            return False
+        r.read_slot, r.pair_slot, r.status, r.t_admit = rs, ps, "admitted", now
+        return True
+
+    def run(self, requests: list, clock=time.perf_counter, idle_sleep: float = 20e-6) -> list:
+        """Serve `requests` (sorted by arrival) to completion; returns them with
+        status, timings and (if configured) results."""
+        t0 = clock()
+        self.ex.start(t0)
+        pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
+        admitted = collections.deque()
+        inflight = collections.deque()
+        free_slots = collections.deque(range(self.cfg.n_streams))
+        while pending or admitted or inflight:
+            now = clock() - t0
+            while inflight and self.ex.done(inflight[0].handle):
+                self._complete(inflight.popleft(), clock() - t0, free_slots)
+            if inflight and now - inflight[0].t_dispatch > self.cfg.round_timeout_s:
+                rnd = inflight[0]
+                for r in rnd.requests:
+                    r.status, r.error = "failed", "round did not complete before the watchdog limit"
+                raise TimeoutError(f"round of {len(rnd.requests)} requests exceeded "
+                                   f"{self.cfg.round_timeout_s} s; the server stopped")
+            while pending and pending[0].arrival <= now:
+                r = pending[0]
+                if r.status == "cancelled":
+                    pending.popleft()
+                    continue
+                if not self.fits_at_all(r):
+                    r.status, r.error = "rejected", "request larger than the server's rings or limits"
+                    pending.popleft()
+                    continue
+                if not self._admit(r, now):
+                    break  # wait for memory: FIFO, no overtaking
+                admitted.append(pending.popleft())
+            if admitted and free_slots:
+                batch, total = [], 0
+                while admitted and total + admitted[0].n_pairs <= self.cfg.max_round_pairs:
+                    total += admitted[0].n_pairs
+                    batch.append(admitted.popleft())
+                slot = free_slots.popleft()
+                rnd = Round(batch, slot, t_dispatch=clock() - t0)
+                for r in batch:
+                    r.status, r.t_dispatch = "running", rnd.t_dispatch
+                rnd.handle = self.ex.launch(batch, slot)
+                inflight.append(rnd)
+                self.rounds_launched += 1
+                self.coalesced.append(len(batch))
+                self.max_inflight_seen = max(self.max_inflight_seen, len(inflight))
+                continue
+            if not (pending and pending[0].arrival <= now):
+                time.sleep(idle_sleep)
+        return requests
+
+    def _complete(self, rnd: Round, now: float, free_slots):
+        dev_t = self.ex.device_done_time(rnd.handle)
+        for r in rnd.requests:
+            r.t_done = now
+            r.t_device_done = dev_t
+            if self.cfg.copy_results:
+                r.accept, r.edits = self.ex.results(r)
+            r.status = "done"
+            self.read_ring.release_oldest()
+            self.pair_ring.release_oldest()
+        free_slots.append(rnd.slot)
+
+
+def latency_summary(requests: list) -> dict:
+    done = [r for r in requests if r.status == "done"]
+    if not done:
+        return {"done": 0}
+    host = np.array([r.t_done - r.arrival for r in done]) * 1e3
+    dev = np.array([r.t_device_done - r.arrival for r in done]) * 1e3
+    pairs = sum(r.n_pairs for r in done)
+    span = max(r.t_done for r in done) - min(r.arrival for r in done)
+    return {"done": len(done), "pairs": pairs, "gpairs_s": pairs / span / 1e9 if span > 0 else None,
+            "p50_ms": float(np.percentile(host, 50)), "p99_ms": float(np.percentile(host, 99)),
+            "max_ms": float(host.max()), "device_p50_ms": float(np.percentile(dev, 50)),
+            "device_p99_ms": float(np.percentile(dev, 99))}
+
+
+class GpuExecutor:
+    """Device rings, per-stream workspaces and the library calls of a round."""
+
+    def __init__(self, ref, config: ServeConfig, device=None):
+        import torch
+
+        from . import gk
+
+        self.torch, self.gk, self.cfg, self.ref = torch, gk, config, ref
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.dev = dev
+        self.sw = config.stride_words
+        if 32 * self.sw < config.max_read_len:
+            raise ValueError("stride_words too small for max_read_len")
+        free, _ = torch.cuda.mem_get_info(dev)
+        budget = int(free * config.mem_fraction)
+        if config.mem_cap_bytes is not None:
+            budget = min(budget, int(config.mem_cap_bytes))
+        ws_bytes = max(256, gk.gk_filter_batched_workspace(config.max_round_pairs))
+        per_read = 8 * self.sw + 3
+        per_pair = 12
+        unit = per_read + per_pair * config.pairs_per_read
+        rest = budget - config.n_streams * ws_bytes
+        if rest < unit * 16:
+            raise MemoryError(f"device budget {budget} B too small for the rings")
+        self.n_read_slots = int(rest // unit)
+        self.n_pair_slots = int(self.n_read_slots * config.pairs_per_read)
+        self.ring_bytes = self.n_read_slots * per_read + self.n_pair_slots * per_pair
+        e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)
+        self.packed = e(self.n_read_slots * self.sw * 2, torch.int32)
+        self.lens = e(self.n_read_slots, torch.int16)
+        self.nflag = e(self.n_read_slots, torch.uint8)
+        self.pread = e(self.n_pair_slots, torch.int32)
+        self.poff = e(self.n_pair_slots, torch.int32)
+        self.pe = e(self.n_pair_slots, torch.uint8)
+        self.acc = e(self.n_pair_slots, torch.uint8)
+        self.ed = e(self.n_pair_slots, torch.int16)
+        self.h_acc = torch.empty(self.n_pair_slots, dtype=torch.uint8, pin_memory=True)
+        self.h_ed = torch.empty(self.n_pair_slots, dtype=torch.int16, pin_memory=True)
+        self.streams = [torch.cuda.Stream(dev) for _ in range(config.n_streams)]
+        self.ws = [e(ws_bytes, torch.uint8) for _ in range(config.n_streams)]
+        self.max_req_per_round = max_req = 65536
+        # per stream slot: seg_end | seg_delta (int64) and seg_e (uint8), host staging and device copies
+        self.h_seg = [torch.empty(2 * max_req, dtype=torch.int64, pin_memory=True) for _ in self.streams]
+        self.h_sege = [torch.empty(max_req, dtype=torch.uint8, pin_memory=True) for _ in self.streams]
+        self.d_seg = [e(2 * max_req, torch.int64) for _ in self.streams]
+        self.d_sege = [e(max_req, torch.uint8) for _ in self.streams]
+        self.tiling = gk.Tiling(*config.tiling)
+        self.ev0 = None
+
+    def start(self, t0):
+        self.ev0 = self.torch.cuda.Event(enable_timing=True)
+        self.ev0.record(self.streams[0])
+        self.t0 = t0
+
+    def launch(self, batch, slot):
+        torch, gk = self.torch, self.gk
+        st = self.streams[slot]
+        sw8 = self.sw * 8
+        M = self.max_req_per_round
+        if len(batch) > M:
+            raise ValueError("too many requests in one round")
+        # pair runs contiguous in the ring, each with its per-request segments
+        runs = []  # [pair_start, n_pairs, seg_index_start, n_segs]
+        hseg = self.h_seg[slot].numpy()
+        hsege = self.h_sege[slot].numpy()
+        dst, src, nb = [], [], []
+        for k, r in enumerate(batch):
+            dst += [self.packed.data_ptr() + r.read_slot * sw8, self.nflag.data_ptr() + r.read_slot,
+                    self.lens.data_ptr() + 2 * r.read_slot, self.pread.data_ptr() + 4 * r.pair_slot,
+                    self.poff.data_ptr() + 4 * r.pair_slot]
+            src += [r.packed.ctypes.data, r.nflag.ctypes.data, r.lens.ctypes.data, r.pair_read.ctypes.data,
+                    r.pair_off.ctypes.data]
+            nb += [r.n_reads * sw8, r.n_reads, 2 * r.n_reads, 4 * r.n_pairs, 4 * r.n_pairs]
+            if runs and runs[-1][0] + runs[-1][1] == r.pair_slot:
+                runs[-1][1] += r.n_pairs
+                runs[-1][3] += 1
+            else:
+                runs.append([r.pair_slot, r.n_pairs, k, 1])
+            hseg[k] = runs[-1][1]          # cumulative end inside its run
+            hseg[M + k] = r.read_slot      # relative ids -> ring slots
+            hsege[k] = r.e
+        n = len(batch)
+        dseg, dsege = self.d_seg[slot], self.d_sege[slot]
+        dst += [dseg.data_ptr(), dseg.data_ptr() + 8 * M, dsege.data_ptr()]
+        src += [self.h_seg[slot].data_ptr(), self.h_seg[slot].data_ptr() + 8 * M, self.h_sege[slot].data_ptr()]
+        nb += [8 * n, 8 * n, n]
+        gk.gk_copy_many(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), gk.H2D, st)
+        for p0, np_, k0, ns in runs:
+            gk.gk_rebase_pairs(self.pread[p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
+                               pair_e=self.pe[p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
+            gk.gk_filter_batched(self.ref, self.packed, self.sw, self.n_read_slots, self.lens, self.nflag,
+                                 self.pread[p0:p0 + np_], self.poff[p0:p0 + np_], self.pe[p0:p0 + np_],
+                                 self.tiling, self.ws[slot], accept=self.acc[p0:p0 + np_],
+                                 edits=self.ed[p0:p0 + np_], stream=st)
+        ev_dev = torch.cuda.Event(enable_timing=True)
+        ev_dev.record(st)
+        dst, src, nb = [], [], []
+        for p0, np_, _, _ in runs:
+            dst += [self.h_acc.data_ptr() + p0, self.h_ed.data_ptr() + 2 * p0]
+            src += [self.acc.data_ptr() + p0, self.ed.data_ptr() + 2 * p0]
+            nb += [np_, 2 * np_]
+        gk.gk_copy_many(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), gk.D2H, st)
+        ev_host = torch.cuda.Event(enable_timing=False)
+        ev_host.record(st)
+        return (ev_dev, ev_host)
+
+    def done(self, handle) -> bool:
+        return handle[1].query()
+
+    def device_done_time(self, handle) -> float:
+        return self.ev0.elapsed_time(handle[0]) * 1e-3
+
+    def results(self, r: Request):
+        a = self.h_acc.numpy()[r.pair_slot:r.pair_slot + r.n_pairs].copy()
+        e = self.h_ed.numpy()[r.pair_slot:r.pair_slot + r.n_pairs].view(np.uint16).copy()
+        return a, e
+
+
+class RequestPool:
+    """Pinned host payloads that requests are cut from: per read length, reads
+    sampled from the genome with their candidates (one true origin, the rest
+    random), encoded once by the library's host encoder (as a client
+    sending host-encoded reads would)."""
+
+    def __init__(self, ref_ascii: np.ndarray, lengths=(100, 150, 250), reads_per_len: int = 260_000,
+                 cands: int = 4, stride_words: int = 8, seed: int = 2103_14978 + 4, pin: bool = True,
+                 keep_ascii: bool = False):
+        import torch
+
+        from . import gk, synth
+
+        self.sw, self.cands, self.pin = stride_words, cands, pin
+        self.by_len = {}
+        for m in lengths:
+            w = synth.pairs_workload(f"pool-{m}", seed=seed + m, ref=ref_ascii, n_pairs=reads_per_len * cands,
+                                     m=m, cands=cands, e=0, read_edit_rate=0.02)
+            packed, nflag = gk.gk_encode(torch.from_numpy(w.reads), w.n_reads, w.stride, fixed_len=m,
+                                         stride_words=stride_words)
+            self.by_len[m] = self._pin(pin, packed=packed.numpy().view(np.uint32), nflag=nflag.numpy(),
+                                       lens=np.full(w.n_reads, m, np.uint16), pair_read=w.pair_read,
+                                       pair_off=w.pair_off)
+            if keep_ascii:
+                self.by_len[m]["ascii"] = (None, w.reads.reshape(w.n_reads, w.stride))
+        # The pool's pairs are grouped by read, `cands` per read, so the ids of
+        # any slice relative to its first read are k // cands: one array serves
+        # every request.
+        max_pairs = cands * max(p["lens"][1].shape[0] for p in self.by_len.values())
+        self.rel_ids = self._pin(pin, a=(np.arange(max_pairs, dtype=np.uint32) // cands))["a"]
+
+    @staticmethod
+    def _pin(pin, **arrays):
+        out = {}
+        for k, a in arrays.items():
+            if pin:
+                import torch
+
+                t = torch.empty(a.shape, dtype=getattr(torch, {"uint8": "uint8", "uint16": "int16",
+                                                                 "uint32": "int32"}[a.dtype.name]),
+                                pin_memory=True)
+                v = t.numpy().view(a.dtype)
+                v[...] = a
+                out[k] = (t, v)
+            else:
+                out[k] = (None, np.ascontiguousarray(a))
+        return out
+
+    def request(self, rid: int, m: int, e: int, n_pairs: int, start_read: int, arrival: float) -> Request:
+        """Cut a request of n_pairs pairs (rounded up to whole reads) of length m
+        starting at pool read `start_read`."""
+        p = self.by_len[m]
+        n_reads = -(-n_pairs // self.cands)
+        total = p["lens"][1].shape[0]
+        r0 = start_read % max(1, total - n_reads)
+        r1 = r0 + n_reads
+        n = n_reads * self.cands
+        w2 = self.sw * 2
+        return Request(id=rid, packed=p["packed"][1][r0 * w2:r1 * w2], nflag=p["nflag"][1][r0:r1],
+                       lens=p["lens"][1][r0:r1], pair_read=self.rel_ids[1][:n],
+                       pair_off=p["pair_off"][1][r0 * self.cands:r1 * self.cands], e=e, arrival=arrival,
+                       max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None)
+
+
+def poisson_plan(n_requests: int, rate_per_s: float, seed: int, size_lo=1_000, size_hi=1_000_000,
+                 lengths=(100, 150, 250), rates=(0.02, 0.05, 0.10)):
+    """Arrival times (Poisson) and request shapes of the serving
+    configuration: log-uniform sizes, a read length and one
+    e = ceil(rate x m) per request."""
+    rng = np.random.default_rng([seed, n_requests, 7])
+    gaps = rng.exponential(1.0 / rate_per_s, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sizes = np.exp(rng.uniform(np.log(size_lo), np.log(size_hi), n_requests)).astype(np.int64)
+    ms = np.asarray(lengths)[rng.integers(0, len(lengths), n_requests)]
+    rs = np.asarray(rates)[rng.integers(0, len(rates), n_requests)]
+    es = np.ceil(np.round(rs * ms, 9)).astype(np.int64)
+    starts = rng.integers(0, 1 << 30, n_requests)
+    return [dict(id=i, arrival=float(arrivals[i]), n_pairs=int(sizes[i]), m=int(ms[i]), e=int(es[i]),
+                 start=int(starts[i])) for i in range(n_requests)]

@@ -1,0 +1,72 @@
+"""The serving loop on the GPU: every request's results are the same served
+alone and in the coalesced mix (tolerance 0), and equal the oracle; memory
+admission under a small device budget."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2103_14978_gb300 import gk, serve, synth
+from tests.gpu_helpers import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    require_gpu()
+    ref = synth.reference(20_000_000, 51, 0.05, 0.001)
+    gkref = gk.gk_load_reference(ref)
+    pool = serve.RequestPool(ref, lengths=(100, 150, 250), reads_per_len=60_000, keep_ascii=True)
+    return ref, gkref, pool
+
+
+def requests(pool, n, rate, seed, size_hi=200_000):
+    plan = serve.poisson_plan(n, rate, seed, size_lo=1_000, size_hi=size_hi)
+    return [pool.request(p["id"], p["m"], p["e"], p["n_pairs"], p["start"], p["arrival"]) for p in plan]
+
+
+def oracle_of(ref, r):
+    rows = np.ascontiguousarray(r.ascii).reshape(-1)
+    starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
+    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, r.pair_read, r.pair_off, r.e)
+    return a, e
+
+
+def test_same_result_alone_and_in_the_mix(setup):
+    ref, gkref, pool = setup
+    cfg = serve.ServeConfig(mem_cap_bytes=3 << 30, max_round_pairs=2_000_000)
+    ex = serve.GpuExecutor(gkref, cfg)
+    mix = requests(pool, 300, 20_000.0, 61)
+    srv = serve.Server(ex, cfg)
+    srv.run(mix)
+    assert all(r.status == "done" for r in mix)
+    assert max(srv.coalesced) > 1, "no round coalesced several requests"
+    summ = serve.latency_summary(mix)
+    assert summ["done"] == 300 and summ["p99_ms"] >= summ["p50_ms"] > 0
+    again = requests(pool, 300, 20_000.0, 61)
+    for r in again[::15]:
+        r.arrival = 0.0
+        serve.Server(ex, cfg).run([r])
+        m = mix[r.id]
+        assert np.array_equal(r.accept, m.accept) and np.array_equal(r.edits, m.edits), r.id
+    for r in sorted(mix, key=lambda q: q.n_pairs)[:40]:
+        a, e = oracle_of(ref, r)
+        assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits), r.id
+
+
+def test_admission_under_a_small_memory_budget(setup):
+    ref, gkref, pool = setup
+    cfg = serve.ServeConfig(mem_cap_bytes=7 << 20, max_round_pairs=150_000)
+    ex = serve.GpuExecutor(gkref, cfg)
+    assert ex.n_pair_slots < 200_000
+    reqs = requests(pool, 120, 50_000.0, 62, size_hi=300_000)
+    srv = serve.Server(ex, cfg)
+    srv.run(reqs)
+    too_big = [r for r in reqs if r.n_pairs > min(ex.n_pair_slots, 150_000) or r.n_reads > ex.n_read_slots]
+    assert too_big and all(r.status == "rejected" for r in too_big)
+    served = [r for r in reqs if r.status == "done"]
+    assert len(served) == len(reqs) - len(too_big)
+    for r in served[::10]:
+        a, e = oracle_of(ref, r)
+        assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits), r.id

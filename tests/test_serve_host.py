@@ -1,0 +1,157 @@
+"""Host logic of the serving loop, on the CPU: the FIFO ring allocator, memory
+admission, coalescing, rejection, cancellation and the watchdog, driven by a
+fake executor on a simulated clock whose results come from the oracle."""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2103_14978_gb300 import serve, synth
+
+
+def test_fifo_ring_never_overlaps():
+    rng = random.Random(4)
+    for size in (1, 7, 64, 1000):
+        ring = serve.FifoRing(size)
+        live = []
+        for _ in range(3000):
+            if live and (rng.random() < 0.45 or not ring.free_slots()):
+                ring.release_oldest()
+                live.pop(0)
+                continue
+            n = rng.randint(1, max(1, size // 3))
+            start = ring.alloc(n)
+            if start is None:
+                assert ring.free_slots() < size  # refusals only when something is live
+                continue
+            assert 0 <= start and start + n <= size
+            for s, k in live:
+                assert start + n <= s or s + k <= start, "overlap"
+            live.append((start, n))
+        with pytest.raises(ValueError):
+            ring.alloc(size + 1)
+
+
+def test_fifo_ring_wraps_and_frees():
+    ring = serve.FifoRing(10)
+    assert ring.alloc(6) == 0
+    assert ring.alloc(3) == 6
+    assert ring.alloc(2) is None          # 1 slot at the end, 0 at the start
+    ring.release_oldest()                 # frees 0..5
+    assert ring.alloc(2) == 0             # skips the one-slot gap at the end
+    assert ring.alloc(5) is None          # 2..5 free: only 4 slots before the tail at 6
+    assert ring.alloc(4) == 2
+    ring.undo_last()
+    assert ring.alloc(4) == 2
+
+
+class FakeExecutor:
+    """Completes a round `delay` simulated seconds after its launch; results
+    from the oracle on the request's own reads and the genome."""
+
+    def __init__(self, genome, n_read_slots, n_pair_slots, delay=0.005, never=False):
+        self.genome = genome
+        self.n_read_slots, self.n_pair_slots = n_read_slots, n_pair_slots
+        self.delay, self.never = delay, never
+        self.now = 0.0
+        self.out = {}
+        self.launches = []
+
+    def start(self, t0):
+        self.t0 = t0
+
+    def launch(self, batch, slot):
+        self.launches.append([r.id for r in batch])
+        for r in batch:
+            rows = np.ascontiguousarray(r.ascii).reshape(-1)
+            starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
+            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, r.pair_read, r.pair_off, r.e)
+            self.out[r.id] = (a, e)
+        return self.now + self.delay
+
+    def done(self, handle):
+        return not self.never and self.now >= handle
+
+    def device_done_time(self, handle):
+        return handle
+
+    def results(self, r):
+        return self.out[r.id]
+
+
+class SimClock:
+    def __init__(self, ex, step=1e-4):
+        self.ex, self.t, self.step = ex, 0.0, step
+
+    def __call__(self):
+        self.t += self.step
+        self.ex.now = self.t
+        return self.t
+
+
+@pytest.fixture(scope="module")
+def pool():
+    ref = synth.reference(300_000, 17, 0.05, 0.0)
+    return ref, serve.RequestPool(ref, lengths=(60, 100), reads_per_len=3000, stride_words=4, pin=False,
+                                  keep_ascii=True)
+
+
+def make_requests(pool_, n, seed, size_hi=4000, spread=0.01):
+    _, p = pool_
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        m = int(rng.choice([60, 100]))
+        reqs.append(p.request(i, m, int(rng.integers(0, 8)), int(rng.integers(1, size_hi)),
+                              int(rng.integers(0, 1 << 20)), float(rng.uniform(0, spread))))
+    return reqs
+
+
+def serve_with(pool_, reqs, n_read_slots=100_000, n_pair_slots=400_000, **cfg):
+    ref, _ = pool_
+    ex = FakeExecutor(ref, n_read_slots, n_pair_slots, never=cfg.pop("never", False))
+    conf = serve.ServeConfig(stride_words=4, max_read_len=128, **cfg)
+    srv = serve.Server(ex, conf)
+    srv.run(reqs, clock=SimClock(ex), idle_sleep=0)
+    return srv, ex
+
+
+def test_every_request_served_and_identical_alone_and_in_the_mix(pool):
+    reqs = make_requests(pool, 40, 1)
+    srv, ex = serve_with(pool, reqs)
+    assert all(r.status == "done" for r in reqs)
+    assert max(len(b) for b in ex.launches) > 1          # coalesced rounds
+    assert srv.max_inflight_seen <= 2
+    for r in reqs:
+        alone = make_requests(pool, 40, 1)[r.id]
+        serve_with(pool, [alone])
+        assert np.array_equal(alone.accept, r.accept) and np.array_equal(alone.edits, r.edits)
+        assert r.t_done >= r.t_device_done >= r.arrival
+
+
+def test_memory_admission_waits_and_rejects(pool):
+    reqs = make_requests(pool, 30, 2, size_hi=3000)
+    big = pool[1].request(99, 100, 3, 5000, 0, 0.0)  # 1250 reads > ring of 800 slots
+    srv, ex = serve_with(pool, reqs + [big], n_read_slots=800, n_pair_slots=3200)
+    assert big.status == "rejected"
+    assert all(r.status == "done" for r in reqs)
+    # rings never held more than their size: every launch fits
+    for ids in ex.launches:
+        assert sum(reqs[i].n_pairs for i in ids) <= 3200
+
+
+def test_cancelled_requests_are_skipped(pool):
+    reqs = make_requests(pool, 10, 4, spread=1.0)
+    reqs[3].cancel()
+    reqs[7].cancel()
+    serve_with(pool, reqs)
+    assert reqs[3].status == reqs[7].status == "cancelled"
+    assert sum(r.status == "done" for r in reqs) == 8
+
+
+def test_watchdog_stops_a_round_that_never_completes(pool):
+    reqs = make_requests(pool, 3, 5)
+    with pytest.raises(TimeoutError):
+        serve_with(pool, reqs, never=True, round_timeout_s=0.05)
+    assert any(r.status == "failed" for r in reqs)
