@@ -19,7 +19,8 @@
 //   - the edge OR of Sec. 3.4 sets, after amendment, the k vacated positions
 //     of mask +k (the low end) and of mask -k (the high end).  The vacated
 //     sets are kept as two incremental bit vectors and folded into the AND:
-//     acc &= eroded | edge is one 3-input logic op;
+//     acc &= eroded | edge is one 3-input logic op.  With k < 32 the low set
+//     lives in word 0 and the high set in the top two words only;
 //   - the AND of the 2e+1 masks stays in registers; the count of the final
 //     vector is per-window runs (a 1 starts a run unless the bit below it is
 //     1 and in the same 4-base window) or a popcount (Sec. 2.1).
@@ -57,93 +58,72 @@ __device__ __forceinline__ void amend_and(const uint32_t (&d)[W], uint32_t (&acc
   }
 }
 
+// Inputs of one pair.
 template <int W>
-__device__ __forceinline__ void diff_mask(const uint32_t (&sh)[W], const uint32_t (&sl)[W],
-                                          const uint32_t (&gh)[W], const uint32_t (&gl)[W],
-                                          uint32_t lastmask, uint32_t (&d)[W]) {
+struct PairData {
+  uint32_t rid, off, e;
+  int status;     // 0 filter, 1 undefined, 2 invalid
+  uint32_t nflag; // read's N flag
+  uint2 ni;       // N index word of the window start
+  uint2 r[W];     // read words
+  uint2 g[W + 1]; // reference words covering the window
+};
+
+template <int W>
+__device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairData<W> &x) {
+  x.rid = a.pair_read[p];
+  x.off = a.pair_off[p];
+  x.e = a.pair_e ? (uint32_t)a.pair_e[p] : a.fixed_e;
+  x.status = ((uint64_t)x.rid >= a.n_reads || (uint64_t)x.off + a.m > a.ref_len) ? 2 : 0;
+  x.nflag = 0;
+  x.ni = make_uint2(0, 0xffffffffu);
+  if (x.status == 0 && a.m > 0) {
+    if (a.read_nflag) x.nflag = a.read_nflag[x.rid];
+    if (a.ref_nidx) x.ni = a.ref_nidx[x.off >> 5];
+    const uint2 *rp = a.reads + (uint64_t)x.rid * a.stride_words;
+    const uint2 *gp = a.ref_hl + (x.off >> 5);
 #pragma unroll
-  for (int w = 0; w < W; ++w) d[w] = (sh[w] ^ gh[w]) | (sl[w] ^ gl[w]);
-  d[W - 1] &= lastmask;
+    for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+#pragma unroll
+    for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+  }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kFilterThreads) filter_kernel(const FilterArgs a) {
-  const uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const bool active = p < a.n_pairs;
-  uint32_t rid = 0, off = 0, e = 0;
-  int status = 0;  // 0 filter, 1 undefined (N), 2 invalid
-  if (active) {
-    rid = a.pair_read[p];
-    off = a.pair_off[p];
-    e = a.pair_e ? (uint32_t)a.pair_e[p] : a.fixed_e;
-    if ((uint64_t)rid >= a.n_reads || (uint64_t)off + a.m > a.ref_len) status = 2;
-  }
-  if (a.err_count) {
-    const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
-    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.err_count, (unsigned)__popc(bad));
-  }
-  if (!active) return;
+// Filters one loaded pair; returns the count.
+template <int W, bool SMALL_K>
+__device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const PairData<W> &x) {
   const uint32_t m = a.m;
-  if (status == 0 && m > 0) {
-    if (a.read_nflag && a.read_nflag[rid]) {
-      status = 1;
-    } else if (a.ref_nidx) {
-      const uint2 ni = a.ref_nidx[off >> 5];
-      const uint32_t q = ni.x >> (off & 31);
-      const uint64_t first = q ? (uint64_t)off + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
-      if (first < (uint64_t)off + m) status = 1;
-    }
-  }
-  if (status != 0 || m == 0) {
-    a.accept[p] = status != 2;
-    a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
-    return;
-  }
-
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 
-  // Read planes (zero past m).
-  uint32_t rh[W], rl[W];
-  const uint2 *rp = a.reads + (uint64_t)rid * a.stride_words;
+  uint32_t rh[W], rl[W], gh[W], gl[W];
+  const uint32_t sh = x.off & 31;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    const uint2 v = rp[w];
-    rh[w] = v.x;
-    rl[w] = v.y;
+    rh[w] = x.r[w].x;
+    rl[w] = x.r[w].y;
+    gh[w] = __funnelshift_r(x.g[w].x, x.g[w + 1].x, sh);
+    gl[w] = __funnelshift_r(x.g[w].y, x.g[w + 1].y, sh);
   }
+  // Both sequences zero past m: the Hamming and -k masks need no masking.
   rh[W - 1] &= lastmask;
   rl[W - 1] &= lastmask;
-
-  // Window planes: bases [off, off+m) funnel-shifted out of words off/32 ...
-  uint32_t gh[W], gl[W];
-  {
-    const uint2 *gp = a.ref_hl + (off >> 5);
-    const uint32_t sh = off & 31;
-    uint2 cur = gp[0];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const uint2 nxt = gp[w + 1];
-      gh[w] = __funnelshift_r(cur.x, nxt.x, sh);
-      gl[w] = __funnelshift_r(cur.y, nxt.y, sh);
-      cur = nxt;
-    }
-  }
+  gh[W - 1] &= lastmask;
+  gl[W - 1] &= lastmask;
 
   uint32_t acc[W], d[W], zero[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     acc[w] = 0xffffffffu;
     zero[w] = 0;
+    d[w] = (rh[w] ^ gh[w]) | (rl[w] ^ gl[w]);
   }
-  // Shift 0: the Hamming mask, amended, no edge.
-  diff_mask<W>(rh, rl, gh, gl, lastmask, d);
-  amend_and<W>(d, acc, zero);
+  amend_and<W>(d, acc, zero);  // shift 0: the Hamming mask, no edge
 
-  const uint32_t kmax = min(e, m - 1);
+  const uint32_t kmax = min(x.e, m - 1);
+  const bool edge_on = a.edge_on != 0;
   if (kmax > 0) {
     uint32_t ph[W], pl[W], nh[W], nl[W], lead[W], trail[W];
-    const bool edge_on = a.edge_on != 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       ph[w] = nh[w] = rh[w];
@@ -159,26 +139,29 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(const FilterArgs
       for (int w = W - 1; w >= 0; --w) {  // +k copy: one base up
         ph[w] = __funnelshift_l(w > 0 ? ph[w - 1] : 0u, ph[w], 1);
         pl[w] = __funnelshift_l(w > 0 ? pl[w - 1] : 0u, pl[w], 1);
-        lead[w] = __funnelshift_l(w > 0 ? lead[w - 1] : lead_fill, lead[w], 1);
+        // vacated low positions [0, k): with k < 32 only word 0 holds them
+        if (!SMALL_K || w == 0) lead[w] = __funnelshift_l(w > 0 ? lead[w - 1] : lead_fill, lead[w], 1);
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) {  // -k copy: one base down
         nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
         nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
-        trail[w] = __funnelshift_r(trail[w], w + 1 < W ? trail[w + 1] : trail_fill, 1);
+        // vacated high positions [m-k, m): with k < 32 only the top two words
+        if (!SMALL_K || w + 2 >= W) trail[w] = __funnelshift_r(trail[w], w + 1 < W ? trail[w + 1] : trail_fill, 1);
       }
-      diff_mask<W>(ph, pl, gh, gl, lastmask, d);
+#pragma unroll
+      for (int w = 0; w < W; ++w) d[w] = (ph[w] ^ gh[w]) | (pl[w] ^ gl[w]);
+      d[W - 1] &= lastmask;  // the +k copy carries read bases past m
       amend_and<W>(d, acc, lead);
-      diff_mask<W>(nh, nl, gh, gl, lastmask, d);
+#pragma unroll
+      for (int w = 0; w < W; ++w) d[w] = (nh[w] ^ gh[w]) | (nl[w] ^ gl[w]);
       amend_and<W>(d, acc, trail);
     }
   }
-  if (a.edge_on == 0 && e >= m) {
+  if (!edge_on && x.e >= m) {
     // Fully vacated masks of the original GateKeeper: window vs code 00.
-    uint32_t zh[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) zh[w] = 0;
-    diff_mask<W>(zh, zh, gh, gl, lastmask, d);
+    for (int w = 0; w < W; ++w) d[w] = gh[w] | gl[w];
     amend_and<W>(d, acc, zero);
   }
 
@@ -188,12 +171,207 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(const FilterArgs
     for (int w = 0; w < W; ++w) count += __popc(acc[w]);
   } else {
 #pragma unroll
+    for (int w = 0; w < W; ++w) count += __popc(acc[w] & ~((acc[w] << 1) & 0xEEEEEEEEu));
+  }
+  return count;
+}
+
+// Deferred-erosion form of filter_loaded for the edge OR on and every shift
+// count k <= 30.  Erosion commutes with AND (the AND of erosions is the
+// erosion of the AND), so the loop ANDs dilated masks only and erodes once at
+// the end.  Mask +k is ORed with its dilated vacated set [-1, k] and mask -k
+// with [m-k-1, m]; that agrees with "erode, then OR the vacated set" at every
+// position except the two next to each vacated run (k and k+1, m-k-2 and
+// m-k-1), where the erosion of the true mask needs two dilation bits the OR
+// hid.  Those bits depend only on the read's first or last two bases against
+// the window and on which window bases are 'A', so their corrections for all
+// k are computed once per pair; so are the two values of the AND one base
+// outside each end that the final erosion reads.
+template <int W>
+__device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, const PairData<W> &x) {
+  const uint32_t m = a.m;
+  const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
+  const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
+
+  uint32_t rh[W], rl[W], gh[W], gl[W];
+  const uint32_t sh = x.off & 31;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    rh[w] = x.r[w].x;
+    rl[w] = x.r[w].y;
+    gh[w] = __funnelshift_r(x.g[w].x, x.g[w + 1].x, sh);
+    gl[w] = __funnelshift_r(x.g[w].y, x.g[w + 1].y, sh);
+  }
+  rh[W - 1] &= lastmask;
+  rl[W - 1] &= lastmask;
+  gh[W - 1] &= lastmask;
+  gl[W - 1] &= lastmask;
+
+  uint32_t acc[W], d[W];
+  // dilation of d into acc (acc &= dil(d) | z), zeros outside the words
+  auto dil_and = [&](const uint32_t (&dd)[W], int which, uint32_t z0, uint32_t zhi, uint32_t zlo) {
+#pragma unroll
     for (int w = 0; w < W; ++w) {
-      const uint32_t f = acc[w];
-      count += __popc(f & ~((f << 1) & 0xEEEEEEEEu));
+      const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
+      const uint32_t above = __funnelshift_r(dd[w], w + 1 < W ? dd[w + 1] : 0u, 1);
+      uint32_t z = 0;
+      if (which == 1 && w == 0) z = z0;
+      if (which == 2 && w == W - 1) z = zhi;
+      if (which == 2 && W >= 2 && w == W - 2) z = zlo;
+      acc[w] &= (dd[w] | below | above) | z;
+    }
+  };
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    acc[w] = 0xffffffffu;
+    d[w] = (rh[w] ^ gh[w]) | (rl[w] ^ gl[w]);
+  }
+  dil_and(d, 0, 0u, 0u, 0u);  // shift 0
+
+  const uint32_t K = min(x.e, m - 1);  // <= 30 on this path
+  {
+    uint32_t ph[W], pl[W], nh[W], nl[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      ph[w] = nh[w] = rh[w];
+      pl[w] = nl[w] = rl[w];
+    }
+    uint32_t lz = 1u;                         // dilated low vacated set: positions 0..k
+    uint32_t tz_hi = ~(lastmask >> 1);        // positions >= m-k-1, top word
+    uint32_t tz_lo = 0u;                      // and the word below it
+    for (uint32_t k = 1; k <= K; ++k) {
+#pragma unroll
+      for (int w = W - 1; w >= 0; --w) {
+        ph[w] = __funnelshift_l(w > 0 ? ph[w - 1] : 0u, ph[w], 1);
+        pl[w] = __funnelshift_l(w > 0 ? pl[w - 1] : 0u, pl[w], 1);
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
+        nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
+      }
+      lz = 2u * lz + 1u;
+      tz_lo = __funnelshift_r(tz_lo, tz_hi, 1);
+      tz_hi = (tz_hi >> 1) | 0x80000000u;
+#pragma unroll
+      for (int w = 0; w < W; ++w) d[w] = (ph[w] ^ gh[w]) | (pl[w] ^ gl[w]);
+      d[W - 1] &= lastmask;
+      dil_and(d, 1, lz, 0u, 0u);
+#pragma unroll
+      for (int w = 0; w < W; ++w) d[w] = (nh[w] ^ gh[w]) | (nl[w] ^ gl[w]);
+      dil_and(d, 2, 0u, tz_hi, tz_lo);
     }
   }
-  a.accept[p] = count <= e;
+
+  // ---- once per pair: end values of the AND, corrections, final erosion ----
+  const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
+  // AND one base below position 0: every non-positive shift compares G[0]
+  // with R[j], j = 0..K.
+  const uint32_t g0h = 0u - (gh[0] & 1u), g0l = 0u - (gl[0] & 1u);
+  const uint32_t q0 = (rh[0] ^ g0h) | (rl[0] ^ g0l);
+  const uint32_t vlo = ((~q0 & rangeK) == 0) ? 1u : 0u;
+  // Top two words as 64-bit windows; bit b is position 32(W-2) + b.
+  const uint64_t GH = ((uint64_t)gh[W - 1] << 32) | (W >= 2 ? gh[W >= 2 ? W - 2 : 0] : 0u);
+  const uint64_t GL = ((uint64_t)gl[W - 1] << 32) | (W >= 2 ? gl[W >= 2 ? W - 2 : 0] : 0u);
+  const uint64_t RH = ((uint64_t)rh[W - 1] << 32) | (W >= 2 ? rh[W >= 2 ? W - 2 : 0] : 0u);
+  const uint64_t RL = ((uint64_t)rl[W - 1] << 32) | (W >= 2 ? rl[W >= 2 ? W - 2 : 0] : 0u);
+  const uint32_t tpos = tail + 32u;  // bit of position m in the 64-bit windows
+  // AND one base above position m-1, needed only when m fills the words:
+  // every non-negative shift compares G[m-1] with R[m-1-j], j = 0..K.
+  uint32_t vtop = 0u;
+  if (tail == 32) {
+    const uint64_t gmh = 0ull - ((GH >> (tpos - 1)) & 1ull), gml = 0ull - ((GL >> (tpos - 1)) & 1ull);
+    const uint64_t qm = (RH ^ gmh) | (RL ^ gml);
+    const uint64_t rng = (((uint64_t)rangeK) << (tpos - 1 - K));
+    vtop = ((~qm & rng) == 0) ? 1u : 0u;
+  }
+  uint32_t f[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t lo_in = w > 0 ? acc[w - 1] : (vlo << 31);
+    const uint32_t hi_in = w + 1 < W ? acc[w + 1] : vtop;
+    f[w] = acc[w] & __funnelshift_l(lo_in, acc[w], 1) & __funnelshift_r(acc[w], hi_in, 1);
+  }
+  // Low-end corrections (positions 1..K+1, word 0).
+  {
+    const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);
+    const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);
+    const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
+    const uint32_t a0 = (gh[0] ^ r0h) | (gl[0] ^ r0l);
+    const uint32_t a1 = ((gh[0] ^ r1h) | (gl[0] ^ r1l)) & v0;
+    const uint32_t vac = gh[0] | gl[0];
+    const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
+    const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
+    const uint32_t r1k = rangeK & ~1u;
+    f[0] &= ~((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));
+  }
+  // High-end corrections (positions m-K-2..m-2, top two words).
+  {
+    const uint64_t b0h = 0ull - ((RH >> (tpos - 1)) & 1ull), b0l = 0ull - ((RL >> (tpos - 1)) & 1ull);
+    const uint64_t b1h = 0ull - ((RH >> (tpos - 2)) & 1ull), b1l = 0ull - ((RL >> (tpos - 2)) & 1ull);
+    const uint64_t B0 = (GH ^ b0h) | (GL ^ b0l);
+    const uint64_t B1 = (GH ^ b1h) | (GL ^ b1l);
+    const uint64_t vac = GH | GL;
+    const uint64_t e1 = (B1 << 1) | B0 | (vac >> 1);
+    const uint64_t e2 = B0 | (vac >> 1) | (vac >> 2);
+    const uint64_t rh_range = ((1ull << (tpos - 1)) - 1ull) & ~((1ull << (tpos - K - 1)) - 1ull);
+    const uint64_t nc = (~(e1 & e2) & rh_range) | ((~e1 & rh_range) >> 1);
+    f[W - 1] &= ~(uint32_t)(nc >> 32);
+    if (W >= 2) f[W >= 2 ? W - 2 : 0] &= ~(uint32_t)nc;
+  }
+  f[W - 1] &= lastmask;
+
+  uint32_t count = 0;
+  if (a.count_mode == GK_COUNT_POPCOUNT) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) count += __popc(f[w]);
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) count += __popc(f[w] & ~((f[w] << 1) & 0xEEEEEEEEu));
+  }
+  return count;
+}
+
+// Resident blocks per SM the compiler must allow: small reads keep enough
+// registers free for 40 warps per SM, which hides the dependent loads of a
+// pair (ids, then read and window words).
+template <int W>
+struct MinBlocks {
+  static constexpr int value = W <= 2 ? 6 : (W <= 4 ? 5 : (W <= 8 ? 2 : 1));
+};
+
+// One thread per pair.  VARIANT 0: any thresholds; 1: every shift count of
+// the launch is < 32; 2: edge OR on and one threshold in 3..30, deferred
+// erosion.
+template <int W, int VARIANT>
+__global__ void __launch_bounds__(kFilterThreads, MinBlocks<W>::value) filter_kernel(const FilterArgs a) {
+  const uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const bool active = p < a.n_pairs;
+  PairData<W> cur;
+  cur.status = 0;
+  if (active) load_pair<W>(a, p, cur);
+  if (a.err_count) {
+    const unsigned bad = __ballot_sync(0xffffffffu, active && cur.status == 2);
+    if (bad && (threadIdx.x & 31) == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
+  }
+  if (!active) return;
+  int status = cur.status;
+  if (status == 0 && a.m > 0) {
+    if (cur.nflag) {
+      status = 1;
+    } else {
+      const uint32_t q = cur.ni.x >> (cur.off & 31);
+      const uint64_t first = q ? (uint64_t)cur.off + (uint32_t)(__ffs(q) - 1) : (uint64_t)cur.ni.y;
+      if (first < (uint64_t)cur.off + a.m) status = 1;
+    }
+  }
+  if (status != 0 || a.m == 0) {
+    a.accept[p] = status != 2;
+    a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+    return;
+  }
+  const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, cur) : filter_loaded<W, VARIANT == 1>(a, cur);
+  a.accept[p] = count <= cur.e;
   a.edits[p] = (uint16_t)count;
 }
 

@@ -3,16 +3,25 @@
 
 namespace gk {
 
-cudaError_t launch_filter_w13_16(int W, const FilterArgs &a, cudaStream_t stream) {
+namespace {
+
+template <int W, int VARIANT>
+cudaError_t launch_one(const FilterArgs &a, cudaStream_t stream) {
   const unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
+  filter_kernel<W, VARIANT><<<blocks, kFilterThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_filter_w13_16(int W, int variant, const FilterArgs &a, cudaStream_t stream) {
   switch (W) {
-    case 13: filter_kernel<13><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 14: filter_kernel<14><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 15: filter_kernel<15><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 16: filter_kernel<16><<<blocks, kFilterThreads, 0, stream>>>(a); break;
+    case 13: return variant == 2 ? launch_one<13, 2>(a, stream) : variant == 1 ? launch_one<13, 1>(a, stream) : launch_one<13, 0>(a, stream);
+    case 14: return variant == 2 ? launch_one<14, 2>(a, stream) : variant == 1 ? launch_one<14, 1>(a, stream) : launch_one<14, 0>(a, stream);
+    case 15: return variant == 2 ? launch_one<15, 2>(a, stream) : variant == 1 ? launch_one<15, 1>(a, stream) : launch_one<15, 0>(a, stream);
+    case 16: return variant == 2 ? launch_one<16, 2>(a, stream) : variant == 1 ? launch_one<16, 1>(a, stream) : launch_one<16, 0>(a, stream);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace gk

@@ -3,16 +3,25 @@
 
 namespace gk {
 
-cudaError_t launch_filter_w1_4(int W, const FilterArgs &a, cudaStream_t stream) {
+namespace {
+
+template <int W, int VARIANT>
+cudaError_t launch_one(const FilterArgs &a, cudaStream_t stream) {
   const unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
+  filter_kernel<W, VARIANT><<<blocks, kFilterThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_filter_w1_4(int W, int variant, const FilterArgs &a, cudaStream_t stream) {
   switch (W) {
-    case 1: filter_kernel<1><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 2: filter_kernel<2><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 3: filter_kernel<3><<<blocks, kFilterThreads, 0, stream>>>(a); break;
-    case 4: filter_kernel<4><<<blocks, kFilterThreads, 0, stream>>>(a); break;
+    case 1: return variant == 2 ? launch_one<1, 2>(a, stream) : variant == 1 ? launch_one<1, 1>(a, stream) : launch_one<1, 0>(a, stream);
+    case 2: return variant == 2 ? launch_one<2, 2>(a, stream) : variant == 1 ? launch_one<2, 1>(a, stream) : launch_one<2, 0>(a, stream);
+    case 3: return variant == 2 ? launch_one<3, 2>(a, stream) : variant == 1 ? launch_one<3, 1>(a, stream) : launch_one<3, 0>(a, stream);
+    case 4: return variant == 2 ? launch_one<4, 2>(a, stream) : variant == 1 ? launch_one<4, 1>(a, stream) : launch_one<4, 0>(a, stream);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace gk

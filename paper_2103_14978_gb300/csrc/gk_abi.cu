@@ -13,10 +13,10 @@
 
 namespace gk {
 
-cudaError_t launch_filter_w1_4(int W, const FilterArgs &a, cudaStream_t stream);
-cudaError_t launch_filter_w5_8(int W, const FilterArgs &a, cudaStream_t stream);
-cudaError_t launch_filter_w9_12(int W, const FilterArgs &a, cudaStream_t stream);
-cudaError_t launch_filter_w13_16(int W, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w1_4(int W, int variant, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w5_8(int W, int variant, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w9_12(int W, int variant, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_w13_16(int W, int variant, const FilterArgs &a, cudaStream_t stream);
 
 namespace {
 thread_local std::string t_last_error;
@@ -35,10 +35,17 @@ int cuda_check(cudaError_t err, const char *what) {
 }
 
 cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
-  if (W >= 1 && W <= 4) return launch_filter_w1_4(W, a, stream);
-  if (W <= 8) return launch_filter_w5_8(W, a, stream);
-  if (W <= 12) return launch_filter_w9_12(W, a, stream);
-  if (W <= 16) return launch_filter_w13_16(W, a, stream);
+  // Every shift count below 32 (one threshold under 32, or reads of at most
+  // 32 bases): the edge vectors live in the end words only.
+  const bool small = (!a.pair_e && a.fixed_e < 32) || a.m <= 32;
+  // Deferred erosion: every shift count <= 30, edge OR on, and enough shifts
+  // (e >= 3) to repay its once-per-pair corrections.
+  const bool deferred = a.edge_on && !a.pair_e && a.fixed_e >= 3 && (a.fixed_e <= 30 || a.m <= 31);
+  const int variant = deferred ? 2 : (small ? 1 : 0);
+  if (W >= 1 && W <= 4) return launch_filter_w1_4(W, variant, a, stream);
+  if (W <= 8) return launch_filter_w5_8(W, variant, a, stream);
+  if (W <= 12) return launch_filter_w9_12(W, variant, a, stream);
+  if (W <= 16) return launch_filter_w13_16(W, variant, a, stream);
   return cudaErrorInvalidValue;
 }
 

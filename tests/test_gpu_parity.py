@@ -173,3 +173,17 @@ def test_config3_structure_scaled(m, es):
     run = GpuRun(w)
     for e in es:
         assert_same(run.filter(e=e), oracle_run(w, e), f"c3 {m}bp scaled e={e}")
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 31, 32, 33, 64, 95, 96, 97, 100, 128, 150, 250, 256, 300])
+def test_every_threshold_3_to_30(m):
+    """One launch per threshold e = 3..30 (the launches whose masks are ANDed
+    dilated and eroded once, with end corrections), word-boundary lengths
+    included, against the oracle; also with N in reads and genome."""
+    w = small_workload(m, 1200, seed=300 + m, n_frac=0.0005, read_n_frac=0.0005)
+    run = GpuRun(w)
+    for e in range(3, 31):
+        assert_same(run.filter(e=e), oracle_run(w, e), f"m={m} e={e}")
+    for e in (4, 17, 30):
+        assert_same(run.filter(e=e, mode=gk.GK_COUNT_POPCOUNT), oracle_run(w, e, O.POPCOUNT),
+                    f"m={m} e={e} popcount")
