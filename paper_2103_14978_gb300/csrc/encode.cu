@@ -15,6 +15,44 @@ namespace {
 
 constexpr int kTileSeqs = 64;    // reads staged in shared memory per block
 constexpr int kEncThreads = 256;
+constexpr int kTileSlack = 64;   // bytes past the tile an unaligned word gather may touch
+
+// Four ASCII bytes -> 4 bits each of the high plane, the low plane and the
+// undefined mask, the first `nvalid` bytes only.  In ASCII, bit 2 of A/C/G/T
+// (either case) is the code's high bit and bit 1 XOR bit 2 its low bit
+// (A=00 C=01 G=10 T=11, Sec. 2.1); a byte is valid iff it equals, case
+// folded, the letter its code names (a byte_perm lookup).  The per-byte bits
+// are gathered into a nibble with one multiply.
+__device__ __forceinline__ void encode4(uint32_t c, uint32_t nvalid, uint32_t &hi4, uint32_t &lo4,
+                                        uint32_t &n4) {
+  const uint32_t hib = (c >> 2) & 0x01010101u;
+  const uint32_t lob = ((c >> 1) ^ (c >> 2)) & 0x01010101u;
+  const uint32_t code = ((c >> 1) & 0x02020202u) | lob;  // per byte 0..3
+  uint32_t sel = (code | (code >> 4)) & 0x00FF00FFu;
+  sel = (sel & 0xFFu) | ((sel >> 8) & 0xFF00u);
+  const uint32_t expect = __byte_perm(0x54474341u, 0u, sel);  // 'A' 'C' 'G' 'T'
+  const uint32_t bad = (c & 0xDFDFDFDFu) ^ expect;
+  const uint32_t nz = (((bad & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | bad) & 0x80808080u;
+  const uint32_t keep = nvalid >= 4 ? 0xFu : ((1u << nvalid) - 1u);
+  n4 = (((nz >> 7) * 0x01020408u) >> 24) & keep;
+  hi4 = (((hib * 0x01020408u) >> 24) & keep) & ~n4;
+  lo4 = (((lob * 0x01020408u) >> 24) & keep) & ~n4;
+}
+
+// 32 bytes (8 little-endian words) -> one {high, low} word and its N bits.
+__device__ __forceinline__ void encode32(const uint32_t (&wb)[8], uint32_t nvalid, uint32_t &hi, uint32_t &lo,
+                                         uint32_t &nb) {
+  hi = lo = nb = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int rem = (int)nvalid - 4 * j;
+    uint32_t h, l, n;
+    encode4(wb[j], rem <= 0 ? 0u : (uint32_t)rem, h, l, n);
+    hi |= h << (4 * j);
+    lo |= l << (4 * j);
+    nb |= n << (4 * j);
+  }
+}
 
 // One block encodes kTileSeqs consecutive reads.  The tile's bytes are one
 // contiguous span of the input, staged into shared memory with 16-byte loads
@@ -46,20 +84,22 @@ encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const ui
   }
   __syncthreads();
   const int total = nseq * (int)stride_words;
+  const uint32_t *t32 = reinterpret_cast<const uint32_t *>(tile);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int s = t / (int)stride_words;
     const int w = t - s * (int)stride_words;
     const uint32_t len = (uint32_t)min_u64(lens ? lens[seq0 + s] : fixed_len, stride);
+    const int64_t rem = (int64_t)len - 32 * (int64_t)w;
     uint32_t hi = 0, lo = 0, nb = 0;
-    const int b0 = w * 32;
-    const int nb_here = (int)min_i64(32, (int64_t)len - b0);
-    const uint8_t *p = tile + (uint64_t)s * stride + b0;
-    for (int b = 0; b < nb_here; ++b) {
-      uint32_t h, l, u;
-      code_of(p[b], h, l, u);
-      hi |= h << b;
-      lo |= l << b;
-      nb |= u;
+    if (rem > 0) {
+      // the word's 32 bytes from 9 aligned shared-memory words
+      const uint64_t o = (uint64_t)s * stride + 32u * (uint64_t)w;
+      const uint32_t *src = t32 + (o >> 2);
+      const uint32_t sh = (uint32_t)(o & 3) * 8u;
+      uint32_t wb[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) wb[j] = __funnelshift_r(src[j], src[j + 1], sh);
+      encode32(wb, rem >= 32 ? 32u : (uint32_t)rem, hi, lo, nb);
     }
     uint32_t *out = packed + ((seq0 + s) * (uint64_t)stride_words + w) * 2;
     *reinterpret_cast<uint2 *>(out) = make_uint2(hi, lo);
@@ -78,31 +118,19 @@ __global__ void encode_contig_kernel(const uint8_t *__restrict__ ascii, uint64_t
   if (w >= n_words) return;
   const uint64_t b0 = w * 32;
   uint32_t hi = 0, lo = 0, nb = 0;
+  uint32_t wb[8];
   if (b0 + 32 <= n_bases && (reinterpret_cast<uintptr_t>(ascii) & 15u) == 0) {
     const uint4 *s4 = reinterpret_cast<const uint4 *>(ascii + b0);
-    uint4 v[2] = {s4[0], s4[1]};
-    const uint32_t *words = reinterpret_cast<const uint32_t *>(v);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t h, l, u;
-        code_of((words[q] >> (8 * j)) & 0xFFu, h, l, u);
-        const int b = q * 4 + j;
-        hi |= h << b;
-        lo |= l << b;
-        nb |= u << b;
-      }
-    }
+    const uint4 v0 = s4[0], v1 = s4[1];
+    wb[0] = v0.x; wb[1] = v0.y; wb[2] = v0.z; wb[3] = v0.w;
+    wb[4] = v1.x; wb[5] = v1.y; wb[6] = v1.z; wb[7] = v1.w;
+    encode32(wb, 32u, hi, lo, nb);
   } else {
     const int n = (int)min_u64(32, n_bases - b0);
-    for (int b = 0; b < n; ++b) {
-      uint32_t h, l, u;
-      code_of(ascii[b0 + b], h, l, u);
-      hi |= h << b;
-      lo |= l << b;
-      nb |= u << b;
-    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) wb[j] = 0;
+    for (int b = 0; b < n; ++b) wb[b >> 2] |= (uint32_t)ascii[b0 + b] << (8 * (b & 3));
+    encode32(wb, (uint32_t)n, hi, lo, nb);
   }
   hl[w] = make_uint2(hi, lo);
   nbits[w] = nb;
@@ -115,7 +143,7 @@ cudaError_t launch_encode_reads(const uint8_t *ascii, uint64_t ascii_stride, con
                                 uint32_t stride_words, uint8_t *nflag, cudaStream_t stream) {
   if (n_seq == 0) return cudaSuccess;
   const uint64_t blocks = (n_seq + kTileSeqs - 1) / kTileSeqs;
-  const size_t smem = (size_t)kTileSeqs * ascii_stride + 16;
+  const size_t smem = (size_t)kTileSeqs * ascii_stride + kTileSlack;
   if (smem > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(encode_reads_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
