@@ -335,44 +335,124 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
 // Resident blocks per SM the compiler must allow: small reads keep enough
 // registers free for 40 warps per SM, which hides the dependent loads of a
 // pair (ids, then read and window words).
-template <int W>
+template <int W, bool COMPACT>
 struct MinBlocks {
-  static constexpr int value = W <= 2 ? 6 : (W <= 4 ? 5 : (W <= 8 ? 2 : 1));
+  static constexpr int value =
+      W <= 2 ? 6 : (W <= 4 ? (COMPACT ? 4 : 5) : (W <= 6 && COMPACT ? 3 : (W <= 8 ? 2 : 1)));
 };
 
-// One thread per pair.  VARIANT 0: any thresholds; 1: every shift count of
-// the launch is < 32; 2: edge OR on and one threshold in 3..30, deferred
-// erosion.
-template <int W, int VARIANT>
-__global__ void __launch_bounds__(kFilterThreads, MinBlocks<W>::value) filter_kernel(const FilterArgs a) {
-  const uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const bool active = p < a.n_pairs;
-  PairData<W> cur;
-  cur.status = 0;
-  if (active) load_pair<W>(a, p, cur);
-  if (a.err_count) {
-    const unsigned bad = __ballot_sync(0xffffffffu, active && cur.status == 2);
-    if (bad && (threadIdx.x & 31) == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
-  }
-  if (!active) return;
-  int status = cur.status;
+// Status of a loaded pair: 0 filter, 1 undefined (N in read or window),
+// 2 invalid.
+template <int W>
+__device__ __forceinline__ int pair_status(const FilterArgs &a, const PairData<W> &x) {
+  int status = x.status;
   if (status == 0 && a.m > 0) {
-    if (cur.nflag) {
+    if (x.nflag) {
       status = 1;
     } else {
-      const uint32_t q = cur.ni.x >> (cur.off & 31);
-      const uint64_t first = q ? (uint64_t)cur.off + (uint32_t)(__ffs(q) - 1) : (uint64_t)cur.ni.y;
-      if (first < (uint64_t)cur.off + a.m) status = 1;
+      const uint32_t q = x.ni.x >> (x.off & 31);
+      const uint64_t first = q ? (uint64_t)x.off + (uint32_t)(__ffs(q) - 1) : (uint64_t)x.ni.y;
+      if (first < (uint64_t)x.off + a.m) status = 1;
     }
   }
-  if (status != 0 || a.m == 0) {
-    a.accept[p] = status != 2;
-    a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+  return status;
+}
+
+__device__ __forceinline__ void write_trivial(const FilterArgs &a, uint64_t p, int status) {
+  a.accept[p] = status != 2;
+  a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+}
+
+template <int W, int VARIANT>
+__device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p, const PairData<W> &x) {
+  const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, x) : filter_loaded<W, VARIANT == 1>(a, x);
+  a.accept[p] = count <= x.e;
+  a.edits[p] = (uint16_t)count;
+}
+
+// Ids, offset, threshold and N information of pair p only (the status phase
+// of the compacting loop).
+__device__ __forceinline__ int classify_pair(const FilterArgs &a, uint64_t p) {
+  const uint32_t rid = a.pair_read[p];
+  const uint32_t off = a.pair_off[p];
+  if ((uint64_t)rid >= a.n_reads || (uint64_t)off + a.m > a.ref_len) return 2;
+  if (a.m == 0) return 3;  // empty read: accept, 0 edits
+  if (a.read_nflag && a.read_nflag[rid]) return 1;
+  if (a.ref_nidx) {
+    const uint2 ni = a.ref_nidx[off >> 5];
+    const uint32_t q = ni.x >> (off & 31);
+    const uint64_t first = q ? (uint64_t)off + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
+    if (first < (uint64_t)off + a.m) return 1;
+  }
+  return 0;
+}
+
+// VARIANT 0: any thresholds; 1: every shift count of the launch is < 32;
+// 2: edge OR on and one threshold in 3..30, deferred erosion.
+//
+// COMPACT false: one thread per pair.  COMPACT true (inputs with many
+// undefined pairs): persistent warps take 32 pairs at a time, write the
+// trivial outcomes at once and queue the pairs that need filtering in a
+// 64-slot per-warp shared queue, filtering 32 queued pairs at a time so that
+// no lane idles next to an undefined pair.
+template <int W, int VARIANT, bool COMPACT>
+__global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) filter_kernel(const FilterArgs a) {
+  if (!COMPACT) {
+    const uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool active = p < a.n_pairs;
+    PairData<W> cur;
+    cur.status = 0;
+    if (active) load_pair<W>(a, p, cur);
+    if (a.err_count) {
+      const unsigned bad = __ballot_sync(0xffffffffu, active && cur.status == 2);
+      if (bad && (threadIdx.x & 31) == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
+    }
+    if (!active) return;
+    const int status = pair_status<W>(a, cur);
+    if (status != 0 || a.m == 0) {
+      write_trivial(a, p, status);
+      return;
+    }
+    filter_and_write<W, VARIANT>(a, p, cur);
     return;
   }
-  const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, cur) : filter_loaded<W, VARIANT == 1>(a, cur);
-  a.accept[p] = count <= cur.e;
-  a.edits[p] = (uint16_t)count;
+  __shared__ uint32_t queue[kFilterThreads / 32][64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t *q = queue[wib];
+  const uint64_t n_chunks = (a.n_pairs + 31) / 32;
+  const uint64_t n_warps = (uint64_t)gridDim.x * (kFilterThreads / 32);
+  uint32_t qn = 0;  // warp-uniform queue length
+  for (uint64_t c = blockIdx.x * (uint64_t)(kFilterThreads / 32) + wib;; c += n_warps) {
+    const bool more = c < n_chunks;
+    if (more) {
+      const uint64_t p = c * 32 + lane;
+      const bool active = p < a.n_pairs;
+      const int status = active ? classify_pair(a, p) : -1;
+      if (a.err_count) {
+        const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
+        if (bad && lane == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
+      }
+      if (status > 0) write_trivial(a, p, status == 3 ? 0 : status);
+      const unsigned need = __ballot_sync(0xffffffffu, status == 0);
+      if ((need >> lane) & 1u) q[qn + __popc(need & ((1u << lane) - 1u))] = (uint32_t)p;
+      qn += __popc(need);
+      __syncwarp();
+    }
+    while (qn >= 32 || (!more && qn > 0)) {
+      const uint32_t take = qn < 32 ? qn : 32;
+      const bool has = (uint32_t)lane < take;
+      const uint32_t pp = has ? q[qn - take + lane] : 0u;
+      __syncwarp();
+      qn -= take;
+      if (has) {
+        PairData<W> cur;
+        load_pair<W>(a, pp, cur);
+        filter_and_write<W, VARIANT>(a, pp, cur);
+      }
+      __syncwarp();
+    }
+    if (!more) break;
+  }
 }
 
 }  // namespace gk

@@ -7,8 +7,25 @@ namespace {
 
 template <int W, int VARIANT>
 cudaError_t launch_one(const FilterArgs &a, cudaStream_t stream) {
-  const unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
-  filter_kernel<W, VARIANT><<<blocks, kFilterThreads, 0, stream>>>(a);
+  unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
+  if (a.compact) {  // persistent warps: a few waves of resident blocks
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel<W, VARIANT, true>,
+                                                                            kFilterThreads, 0);
+      if (err != cudaSuccess) return err;
+      if (per_sm < 1) per_sm = 1;
+    }
+    const uint64_t wave = 4ull * (uint64_t)sms * (uint64_t)per_sm;
+    if (blocks > wave) blocks = (unsigned)wave;
+  }
+  if (a.compact)
+    filter_kernel<W, VARIANT, true><<<blocks, kFilterThreads, 0, stream>>>(a);
+  else
+    filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 

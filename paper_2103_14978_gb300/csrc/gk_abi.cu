@@ -242,6 +242,10 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.accept = accept_out;
   a.edits = edits_out;
   a.err_count = err_count;
+  // A genome with N makes a large share of windows undefined (0.1% N gives
+  // 1 - 0.999^m of them): filter only the defined pairs, in full warps, when
+  // the per-pair work (e >= 3, or per-pair thresholds) repays the queueing.
+  a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 && (pair_e || fixed_e >= 3)) ? 1 : 0;
   return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
 }
 

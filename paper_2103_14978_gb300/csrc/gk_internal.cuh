@@ -59,6 +59,7 @@ struct FilterArgs {
   uint8_t *accept;
   uint16_t *edits;
   uint32_t *err_count;  // nullable
+  int compact;          // plain filter: persistent warps that filter only defined pairs
 };
 
 // Launches the plain filter for words-per-read W = ceil(m/32) (1..16).
