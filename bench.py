@@ -495,7 +495,7 @@ def run_config3(args):
                                      pairs.pair_read, pairs.pair_off, e, accept=acc, edits=ed, stream=stream)
             for _ in range(args.warmup):
                 f()
-            per_e[e] = time_events(torch, f, max(3, args.steps // 10), stream)
+            per_e[e] = time_events(torch, f, args.steps, stream)
         torch.cuda.synchronize()
         undefined = int((dd.edits_u16(ed) == gk.GK_EDITS_UNDEFINED).sum())
         filtered = w.n_pairs - undefined
@@ -548,7 +548,7 @@ def run_config4(args):
     bf.capture()
     for _ in range(args.warmup):
         bf.replay()
-    steps = max(3, args.steps // 10)
+    steps = args.steps
     batched_ms = time_events(torch, bf.replay, steps, stream)
     # plain filter: one launch per read length over pairs grouped by length
     m_pair = w.read_len[w.pair_read]

@@ -147,10 +147,12 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
 
 /* Tiling of the batched filter (chosen by the autotuner). */
 typedef struct {
-  uint32_t words_per_thread; /* words of a pair held per lane: 2, 3, 4, 6 or 8 */
+  uint32_t words_per_thread; /* words of a pair held per lane: 2, 3, 4, 6 or 8;
+                                1 = a whole pair per lane for reads up to 256
+                                bases (4 words per lane above) */
   uint32_t tile_pairs;       /* pairs per tile (work unit of a warp), 32..65536 */
   uint32_t blocks_per_sm;    /* persistent grid = SM count x this, 1..32 */
-  uint32_t warps_per_block;  /* 1..32 */
+  uint32_t warps_per_block;  /* 1..8 */
 } gk_tiling_t;
 
 /* Workspace bytes gk_filter_batched needs for n_pairs pairs (6 bytes per

@@ -19,10 +19,10 @@ import torch
 
 from . import gk
 
-DEFAULT_TILING = (4, 256, 4, 8)
-WPT_CHOICES = (2, 3, 4, 6, 8)
+DEFAULT_TILING = (1, 256, 4, 8)
+WPT_CHOICES = (1, 2, 3, 4, 6, 8)
 TILE_CHOICES = (64, 256, 1024, 4096)
-GRID_CHOICES = ((1, 8), (2, 8), (4, 8), (8, 4), (4, 4), (16, 2))
+GRID_CHOICES = ((1, 8), (2, 8), (3, 8), (4, 8), (8, 4), (4, 4), (16, 2))
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiling_table.json")
 
 

@@ -164,6 +164,7 @@ BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs) {
   return s;
 }
 
+cudaError_t launch_persistent_wpt1(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt2(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt3(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt4(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
@@ -187,6 +188,7 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t grid = (uint32_t)sms * blocks_per_sm;
   switch (wpt) {
+    case 1: return launch_persistent_wpt1(a, grid, warps_per_block, stream);
     case 2: return launch_persistent_wpt2(a, grid, warps_per_block, stream);
     case 3: return launch_persistent_wpt3(a, grid, warps_per_block, stream);
     case 4: return launch_persistent_wpt4(a, grid, warps_per_block, stream);

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "coop.cuh"
+#include "filter.cuh"
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -49,11 +50,46 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
 template <int WPT>
 cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
 
-// Persistent filter body, shared by every WPT instantiation.
+// One pair per lane for a tile of words-per-read W <= 8: the plain filter's
+// per-thread code (deferred erosion when the tile's shift count is 3..30
+// with the edge OR on, exact erosion otherwise), each pair with its own m.
+template <int W>
+__device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t K,
+                                           int lane) {
+  const bool deferred = a.f.edge_on && K >= 3 && K <= 30;
+  for (uint32_t base = first; base < end; base += 32) {
+    const uint32_t slot = base + (uint32_t)lane;
+    if (slot < end) {
+      const uint32_t p = a.s.perm[slot];
+      PairData<W> x;
+      x.rid = a.f.pair_read[p];
+      x.off = a.f.pair_off[p];
+      x.e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
+      x.m = a.read_len[x.rid];
+      x.status = 0;
+      const uint2 *rp = a.f.reads + (uint64_t)x.rid * a.f.stride_words;
+      const uint2 *gp = a.f.ref_hl + (x.off >> 5);
+#pragma unroll
+      for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+#pragma unroll
+      for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+      const uint32_t count = deferred ? filter_loaded_deferred<W>(a.f, x)
+                                      : (K < 32 ? filter_loaded<W, true>(a.f, x) : filter_loaded<W, false>(a.f, x));
+      a.f.accept[p] = count <= x.e;
+      a.f.edits[p] = (uint16_t)count;
+    }
+  }
+}
+
 template <int WPT>
-__global__ void persistent_kernel(const BatchArgs a) {
+__device__ __forceinline__ void tile_coop(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t W, uint32_t K,
+                                          int lane);
+
+// Persistent filter body, shared by every instantiation.  WPT = 1: one pair
+// per lane for tiles with W <= 8, lane groups of 4 words per lane above.
+template <int WPT>
+__global__ void __launch_bounds__(256, WPT == 1 ? 2 : 1) persistent_kernel(const BatchArgs a) {
   const int lane = threadIdx.x & 31;
-  const bool edge_on = a.f.edge_on != 0;
   const uint32_t n_tiles = a.s.counters[1];
   for (;;) {
     uint32_t t = 0;
@@ -70,6 +106,30 @@ __global__ void persistent_kernel(const BatchArgs a) {
     const uint32_t W = key_W(key), K = key_K(key);
     const uint32_t first = a.s.pair_base[lo] + (t - a.s.tile_base[lo]) * a.tile_pairs;
     const uint32_t end = min(first + a.tile_pairs, a.s.pair_base[lo + 1]);
+    if (WPT == 1) {
+      switch (W) {
+        case 1: tile_whole<1>(a, first, end, K, lane); break;
+        case 2: tile_whole<2>(a, first, end, K, lane); break;
+        case 3: tile_whole<3>(a, first, end, K, lane); break;
+        case 4: tile_whole<4>(a, first, end, K, lane); break;
+        case 5: tile_whole<5>(a, first, end, K, lane); break;
+        case 6: tile_whole<6>(a, first, end, K, lane); break;
+        case 7: tile_whole<7>(a, first, end, K, lane); break;
+        case 8: tile_whole<8>(a, first, end, K, lane); break;
+        default: tile_coop<4>(a, first, end, W, K, lane); break;
+      }
+      __syncwarp();
+      continue;
+    }
+    tile_coop<WPT>(a, first, end, W, K, lane);
+  }
+}
+
+template <int WPT>
+__device__ __forceinline__ void tile_coop(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t W, uint32_t K,
+                                          int lane) {
+  const bool edge_on = a.f.edge_on != 0;
+  {
     Group g;
     g.L = (int)((W + WPT - 1) / WPT);
     const int ppw = 32 / g.L;

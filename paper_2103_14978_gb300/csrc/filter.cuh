@@ -61,7 +61,7 @@ __device__ __forceinline__ void amend_and(const uint32_t (&d)[W], uint32_t (&acc
 // Inputs of one pair.
 template <int W>
 struct PairData {
-  uint32_t rid, off, e;
+  uint32_t rid, off, e, m;  // m: this pair's read length
   int status;     // 0 filter, 1 undefined, 2 invalid
   uint32_t nflag; // read's N flag
   uint2 ni;       // N index word of the window start
@@ -74,6 +74,7 @@ __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairD
   x.rid = a.pair_read[p];
   x.off = a.pair_off[p];
   x.e = a.pair_e ? (uint32_t)a.pair_e[p] : a.fixed_e;
+  x.m = a.m;
   x.status = ((uint64_t)x.rid >= a.n_reads || (uint64_t)x.off + a.m > a.ref_len) ? 2 : 0;
   x.nflag = 0;
   x.ni = make_uint2(0, 0xffffffffu);
@@ -92,7 +93,7 @@ __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairD
 // Filters one loaded pair; returns the count.
 template <int W, bool SMALL_K>
 __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const PairData<W> &x) {
-  const uint32_t m = a.m;
+  const uint32_t m = x.m;
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 
@@ -189,7 +190,7 @@ __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const Pai
 // outside each end that the final erosion reads.
 template <int W>
 __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, const PairData<W> &x) {
-  const uint32_t m = a.m;
+  const uint32_t m = x.m;
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 

@@ -271,11 +271,11 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
     return fail(GK_EINVAL, "gk_filter_batched: unknown count_mode");
   if (flags & ~GK_FLAG_NO_EDGE_FIX) return fail(GK_EINVAL, "gk_filter_batched: unknown flags");
   const gk_tiling_t t = *tiling;
-  if (!(t.words_per_thread == 2 || t.words_per_thread == 3 || t.words_per_thread == 4 ||
-        t.words_per_thread == 6 || t.words_per_thread == 8))
-    return fail(GK_EINVAL, "gk_filter_batched: words_per_thread must be 2, 3, 4, 6 or 8");
+  if (!(t.words_per_thread == 1 || t.words_per_thread == 2 || t.words_per_thread == 3 ||
+        t.words_per_thread == 4 || t.words_per_thread == 6 || t.words_per_thread == 8))
+    return fail(GK_EINVAL, "gk_filter_batched: words_per_thread must be 1, 2, 3, 4, 6 or 8");
   if (t.tile_pairs < 32 || t.tile_pairs > 65536 || t.blocks_per_sm < 1 || t.blocks_per_sm > 32 ||
-      t.warps_per_block < 1 || t.warps_per_block > 32)
+      t.warps_per_block < 1 || t.warps_per_block > 8)
     return fail(GK_EINVAL, "gk_filter_batched: tiling out of range");
   if (!workspace || !aligned(workspace, 256) || workspace_bytes < gk::batch_scratch_bytes(n_pairs))
     return fail(GK_EINVAL, "gk_filter_batched: workspace missing, unaligned or too small");

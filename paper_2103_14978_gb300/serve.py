@@ -159,7 +159,7 @@ class ServeConfig:
     mem_cap_bytes: int | None = None  # hard cap on the rings' memory (simulated small device)
     max_round_pairs: int = 4_000_000
     n_streams: int = 2
-    tiling: tuple = (4, 256, 4, 8)
+    tiling: tuple = (1, 256, 3, 8)
     round_timeout_s: float = 30.0     # host watchdog on a launched round
     copy_results: bool = True         # copy each request's results out of the result ring
 

@@ -52,14 +52,14 @@ def mixed():
     return Batched(w), oracle_run(w)
 
 
-@pytest.mark.parametrize("wpt", [2, 3, 4, 6, 8])
+@pytest.mark.parametrize("wpt", [1, 2, 3, 4, 6, 8])
 def test_batched_parity_every_wpt(mixed, wpt):
     b, want = mixed
     _, got = b.filter_((wpt, 256, 2, 8))
     assert_same(got, want, f"batched wpt={wpt}")
 
 
-@pytest.mark.parametrize("tiling", [(4, 32, 1, 1), (2, 65536, 1, 4), (3, 64, 8, 4), (8, 1024, 1, 16)])
+@pytest.mark.parametrize("tiling", [(4, 32, 1, 1), (2, 65536, 1, 4), (3, 64, 8, 4), (8, 1024, 1, 8), (1, 32, 2, 8), (1, 4096, 1, 2)])
 def test_batched_parity_tilings(mixed, tiling):
     b, want = mixed
     _, got = b.filter_(tiling)
