@@ -537,11 +537,14 @@ def run_config4(args):
     samp = np.sort(rng.choice(w.n_pairs, min(w.n_pairs, 4_000_000), replace=False))
     sp = dd.upload_pairs(w.pair_read[samp], w.pair_off[samp], w.pair_e[samp])
     logs = []
-    best, results = batch.autotune(ref, reads.packed, reads.stride_words, reads.n_reads, read_len, reads.nflag,
-                                   sp.pair_read, sp.pair_off, sp.pair_e, reps=2, budget_s=args.tune_seconds,
-                                   log=logs.append)
     sig = batch.signature(w.read_len, w.pair_read, w.pair_e)
-    batch.save_table(batch.table_key(sig), best, results)
+    if args.tune_seconds > 0:
+        best, results = batch.autotune(ref, reads.packed, reads.stride_words, reads.n_reads, read_len,
+                                       reads.nflag, sp.pair_read, sp.pair_off, sp.pair_e, reps=2,
+                                       budget_s=args.tune_seconds, log=logs.append)
+        batch.save_table(batch.table_key(sig), best, results)
+    else:  # no tuning: the recorded tiling for this GPU and workload, else the default
+        best, results = batch.lookup(sig) or batch.DEFAULT_TILING, {}
     del sp
     bf = batch.BatchedFilter(ref, reads.packed, reads.stride_words, reads.n_reads, read_len, reads.nflag,
                              pairs.pair_read, pairs.pair_off, pairs.pair_e, best)

@@ -99,15 +99,16 @@ def autotune(ref, reads, stride_words, n_reads, read_len, read_nflag, pair_read,
              reps: int = 3, budget_s: float = 60.0, log=None):
     """Coordinate search over the tiling on the given (sample) pairs: words
     per lane first, then tile size, then grid shape; every candidate timed with
-    CUDA events, invalid ones (a block that does not fit) skipped.  Returns
-    (best tiling tuple, {candidate: ms})."""
+    CUDA events, invalid ones (a block that does not fit) skipped.  The
+    default tiling is always measured; the budget stops the search after it.
+    Returns (best tiling tuple, {candidate: ms})."""
     t0 = time.perf_counter()
     results = {}
 
-    def measure(t):
+    def measure(t, first=False):
         if t in results:
             return results[t]
-        if time.perf_counter() - t0 > budget_s:
+        if not first and time.perf_counter() - t0 > budget_s:
             return float("inf")
         try:
             bf = BatchedFilter(ref, reads, stride_words, n_reads, read_len, read_nflag, pair_read, pair_off,
@@ -121,7 +122,7 @@ def autotune(ref, reads, stride_words, n_reads, read_len, read_nflag, pair_read,
         return ms
 
     best = DEFAULT_TILING
-    measure(best)
+    measure(best, first=True)
     for wpt in WPT_CHOICES:
         cand = (wpt,) + best[1:]
         if measure(cand) < results[best]:

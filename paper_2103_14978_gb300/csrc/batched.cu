@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(const BatchArgs a) {
     a.s.tile_base[kKeys] = bt;
     a.s.counters[0] = 0;
     a.s.counters[1] = bt;
+    a.s.counters[2] = 0;
+    a.s.counters[3] = 0;
   }
 }
 
@@ -164,7 +166,9 @@ BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs) {
   return s;
 }
 
-cudaError_t launch_persistent_wpt1(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_whole_w1_8(const BatchArgs &a, uint32_t sms, uint32_t bpsm, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_whole_w9_12(const BatchArgs &a, uint32_t sms, uint32_t bpsm, uint32_t wpb, cudaStream_t s);
+cudaError_t launch_whole_w13_16(const BatchArgs &a, uint32_t sms, uint32_t bpsm, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt2(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt3(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
 cudaError_t launch_persistent_wpt4(const BatchArgs &a, uint32_t grid, uint32_t wpb, cudaStream_t s);
@@ -187,8 +191,16 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t grid = (uint32_t)sms * blocks_per_sm;
+  if (wpt == 1) {
+    // One pair per lane: three W ranges, widest first; each launch drains its
+    // own range of tiles.
+    const uint32_t n = (uint32_t)sms;
+    err = launch_whole_w13_16(a, n, blocks_per_sm, warps_per_block, stream);
+    if (err == cudaSuccess) err = launch_whole_w9_12(a, n, blocks_per_sm, warps_per_block, stream);
+    if (err == cudaSuccess) err = launch_whole_w1_8(a, n, blocks_per_sm, warps_per_block, stream);
+    return err;
+  }
   switch (wpt) {
-    case 1: return launch_persistent_wpt1(a, grid, warps_per_block, stream);
     case 2: return launch_persistent_wpt2(a, grid, warps_per_block, stream);
     case 3: return launch_persistent_wpt3(a, grid, warps_per_block, stream);
     case 4: return launch_persistent_wpt4(a, grid, warps_per_block, stream);

@@ -50,9 +50,11 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
 template <int WPT>
 cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
 
-// One pair per lane for a tile of words-per-read W <= 8: the plain filter's
+// One pair per lane over a tile of words-per-read W: the plain filter's
 // per-thread code (deferred erosion when the tile's shift count is 3..30
 // with the edge OR on, exact erosion otherwise), each pair with its own m.
+// Every pair of a tile with K <= 30 has e = K; the code clamps the shift
+// count to m - 1 per pair.
 template <int W>
 __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t K,
                                            int lane) {
@@ -81,14 +83,75 @@ __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, u
   }
 }
 
+template <int W, int WHI>
+__device__ __forceinline__ void dispatch_whole(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t Wt,
+                                               uint32_t K, int lane) {
+  if (Wt == W) {
+    tile_whole<W>(a, first, end, K, lane);
+  } else if constexpr (W < WHI) {
+    dispatch_whole<W + 1, WHI>(a, first, end, Wt, K, lane);
+  }
+}
+
+// Key slot of tile t among slots [s_lo, s_hi): the last slot whose first tile
+// is <= t (slots without tiles share their successor's tile_base).
+__device__ __forceinline__ int slot_of_tile(const BatchArgs &a, uint32_t t, int s_lo, int s_hi) {
+  int lo = s_lo, hi = s_hi - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.s.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One pair per lane over the tiles whose W lies in [WLO, WHI].  In the
+// descending key order those keys are the slots [kKeys - 256 WHI,
+// kKeys - 256 (WLO - 1)), so their tiles form one contiguous range of
+// tile_base; the range has its own tile counter, counters[CTR].  Register
+// use follows the widest W of the range, so ranges are launched separately
+// (widest first) rather than sharing one register budget.
+template <int WLO, int WHI, int CTR>
+__global__ void __launch_bounds__(256, WHI <= 8 ? 2 : 1) whole_kernel(const BatchArgs a) {
+  const int lane = threadIdx.x & 31;
+  constexpr int s_lo = kKeys - 256 * WHI, s_hi = kKeys - 256 * (WLO - 1);
+  const uint32_t t_lo = a.s.tile_base[s_lo], t_hi = a.s.tile_base[s_hi];
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = t_lo + atomicAdd(&a.s.counters[CTR], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= t_hi) break;
+    const int slot = slot_of_tile(a, t, s_lo, s_hi);
+    const uint32_t key = (uint32_t)(kKeys - 1 - slot);
+    const uint32_t first = a.s.pair_base[slot] + (t - a.s.tile_base[slot]) * a.tile_pairs;
+    const uint32_t end = min(first + a.tile_pairs, a.s.pair_base[slot + 1]);
+    dispatch_whole<WLO, WHI>(a, first, end, key_W(key), key_K(key), lane);
+    __syncwarp();
+  }
+}
+
+// Launches whole_kernel<WLO, WHI, CTR> on at most blocks_per_sm blocks per SM
+// (fewer when the register file holds fewer).
+template <int WLO, int WHI, int CTR>
+cudaError_t launch_whole(const BatchArgs &a, uint32_t sms, uint32_t blocks_per_sm, uint32_t wpb,
+                         cudaStream_t s) {
+  int fit = 0;
+  cudaError_t err =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, whole_kernel<WLO, WHI, CTR>, 32 * (int)wpb, 0);
+  if (err != cudaSuccess) return err;
+  if (fit == 0) return cudaErrorInvalidConfiguration;  // block does not fit the register file
+  const uint32_t grid = sms * ((uint32_t)fit < blocks_per_sm ? (uint32_t)fit : blocks_per_sm);
+  whole_kernel<WLO, WHI, CTR><<<grid, 32 * wpb, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int WPT>
 __device__ __forceinline__ void tile_coop(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t W, uint32_t K,
                                           int lane);
 
-// Persistent filter body, shared by every instantiation.  WPT = 1: one pair
-// per lane for tiles with W <= 8, lane groups of 4 words per lane above.
+// Persistent filter body of the lane-group tilings: a pair spread over
+// ceil(W / WPT) lanes.
 template <int WPT>
-__global__ void __launch_bounds__(256, WPT == 1 ? 2 : 1) persistent_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(256, 1) persistent_kernel(const BatchArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles = a.s.counters[1];
   for (;;) {
@@ -96,31 +159,11 @@ __global__ void __launch_bounds__(256, WPT == 1 ? 2 : 1) persistent_kernel(const
     if (lane == 0) t = atomicAdd(&a.s.counters[0], 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= n_tiles) break;
-    // Key of tile t: the last key slot (descending order) whose tile_base <= t.
-    int lo = 0, hi = kKeys - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.s.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t key = (uint32_t)(kKeys - 1 - lo);  // slot 0 is the heaviest key
+    const int slot = slot_of_tile(a, t, 0, kKeys);
+    const uint32_t key = (uint32_t)(kKeys - 1 - slot);  // slot 0 is the heaviest key
     const uint32_t W = key_W(key), K = key_K(key);
-    const uint32_t first = a.s.pair_base[lo] + (t - a.s.tile_base[lo]) * a.tile_pairs;
-    const uint32_t end = min(first + a.tile_pairs, a.s.pair_base[lo + 1]);
-    if (WPT == 1) {
-      switch (W) {
-        case 1: tile_whole<1>(a, first, end, K, lane); break;
-        case 2: tile_whole<2>(a, first, end, K, lane); break;
-        case 3: tile_whole<3>(a, first, end, K, lane); break;
-        case 4: tile_whole<4>(a, first, end, K, lane); break;
-        case 5: tile_whole<5>(a, first, end, K, lane); break;
-        case 6: tile_whole<6>(a, first, end, K, lane); break;
-        case 7: tile_whole<7>(a, first, end, K, lane); break;
-        case 8: tile_whole<8>(a, first, end, K, lane); break;
-        default: tile_coop<4>(a, first, end, W, K, lane); break;
-      }
-      __syncwarp();
-      continue;
-    }
+    const uint32_t first = a.s.pair_base[slot] + (t - a.s.tile_base[slot]) * a.tile_pairs;
+    const uint32_t end = min(first + a.tile_pairs, a.s.pair_base[slot + 1]);
     tile_coop<WPT>(a, first, end, W, K, lane);
   }
 }
