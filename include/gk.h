@@ -155,7 +155,7 @@ typedef struct {
   uint32_t warps_per_block;  /* 1..8 */
 } gk_tiling_t;
 
-/* Workspace bytes gk_filter_batched needs for n_pairs pairs (6 bytes per
+/* Workspace bytes gk_filter_batched needs for n_pairs pairs (20 bytes per
  * pair plus 80 KiB). */
 uint64_t gk_filter_batched_workspace(uint64_t n_pairs);
 
@@ -227,7 +227,7 @@ int gk_copy_many(void *const *dst, const void *const *src, const uint64_t *bytes
  * deployment convenience.
  *
  * Same arguments and results as gk_filter_batched, without the workspace:
- * the scratch is a fixed array inside the library image (about 5.8 MiB per
+ * the scratch is a fixed array inside the library image (about 19.1 MiB per
  * GPU, held by every GPU that loads the library until the process exits).
  * The call allocates nothing.
  *   - n_pairs is limited to GK_NOALLOC_MAX_PAIRS; larger batches return

@@ -1,6 +1,6 @@
 // Planning kernels of the batched filter: classify pairs (trivial outcomes
 // written at once, the rest keyed by (W, K)), scan the key histogram into
-// perm slots and tiles (heaviest key first), scatter pair indices by key.
+// record slots and tiles (heaviest key first), scatter pair records by key.
 #include "batched.cuh"
 
 namespace gk {
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kPlanThreads) classify_kernel(const BatchArgs 
       a.f.accept[p] = status != 2;
       a.f.edits[p] = status == 2 ? GK_EDITS_INVALID : (status == 1 ? GK_EDITS_UNDEFINED : 0);
     }
-    a.s.key[p] = (uint16_t)key;
+    a.s.km[p] = key | (m << 16);
   }
   if (a.f.err_count) {
     const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const BatchArgs a) {
 }
 
 // Each block takes kScatterChunk pairs: a block histogram reserves one range
-// per key in the global cursors, then every pair takes a slot in its range.
+// per key in the global cursors, then every pair writes its record (pair
+// index, read id, offset, e and m) to a slot in its range, so the filter
+// reads pair data in slot order.
 __global__ void __launch_bounds__(kPlanThreads) scatter_kernel(const BatchArgs a) {
   __shared__ uint32_t local[kKeys];
   for (int i = threadIdx.x; i < kKeys; i += blockDim.x) local[i] = 0;
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kPlanThreads) scatter_kernel(const BatchArgs a
   const uint64_t p0 = (uint64_t)blockIdx.x * kScatterChunk;
   const uint64_t p1 = min_u64(p0 + kScatterChunk, a.f.n_pairs);
   for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const uint16_t k = a.s.key[p];
+    const uint32_t k = a.s.km[p] & 0xFFFFu;
     if (k != kNoKey) atomicAdd(&local[k], 1u);
   }
   __syncthreads();
@@ -134,26 +136,28 @@ __global__ void __launch_bounds__(kPlanThreads) scatter_kernel(const BatchArgs a
     if (local[i]) local[i] = atomicAdd(&a.s.cursor[i], local[i]);
   __syncthreads();
   for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const uint16_t k = a.s.key[p];
-    if (k != kNoKey) a.s.perm[atomicAdd(&local[k], 1u)] = (uint32_t)p;
+    const uint32_t km = a.s.km[p];
+    const uint32_t k = km & 0xFFFFu;
+    if (k != kNoKey) {
+      const uint32_t e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : min(a.f.fixed_e, 0xFFFFu);
+      a.s.rec[atomicAdd(&local[k], 1u)] =
+          make_uint4((uint32_t)p, a.f.pair_read[p], a.f.pair_off[p], e | (km & 0xFFFF0000u));
+    }
   }
 }
 
 }  // namespace
 
-uint64_t batch_scratch_bytes(uint64_t n_pairs) {
-  auto up = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
-  return up(2 * n_pairs) + up(4 * n_pairs) + 2 * up(4 * kKeys) + 2 * up(4 * (kKeys + 1)) + up(16);
-}
+uint64_t batch_scratch_bytes(uint64_t n_pairs) { return batch_scratch_size(n_pairs); }
 
 BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs) {
   auto up = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
   char *b = static_cast<char *>(base);
   BatchScratch s;
-  s.key = reinterpret_cast<uint16_t *>(b);
-  b += up(2 * n_pairs);
-  s.perm = reinterpret_cast<uint32_t *>(b);
+  s.km = reinterpret_cast<uint32_t *>(b);
   b += up(4 * n_pairs);
+  s.rec = reinterpret_cast<uint4 *>(b);
+  b += up(16 * n_pairs);
   s.hist = reinterpret_cast<uint32_t *>(b);
   b += up(4 * kKeys);
   s.cursor = reinterpret_cast<uint32_t *>(b);

@@ -23,14 +23,22 @@ __host__ __device__ __forceinline__ uint32_t key_K(uint32_t key) { return key % 
 
 // Scratch of the batched path (all device memory, caller-provided).
 struct BatchScratch {
-  uint16_t *key;        // n_pairs
-  uint32_t *perm;       // n_pairs: pair indices grouped by key
+  uint32_t *km;         // n_pairs: key | m << 16 (key kNoKey: result already written)
+  uint4 *rec;           // n_pairs records grouped by key: {pair index, read id, offset, e | m << 16}
   uint32_t *hist;       // kKeys pair counts
   uint32_t *cursor;     // kKeys scatter cursors
-  uint32_t *pair_base;  // kKeys + 1: first perm slot of each key (descending key order)
+  uint32_t *pair_base;  // kKeys + 1: first record slot of each key (descending key order)
   uint32_t *tile_base;  // kKeys + 1: first tile of each key (descending key order)
-  uint32_t *counters;   // [0] next tile, [1] tile count
+  uint32_t *counters;   // [0] next tile, [1] tile count, [2] [3] next tile of the W ranges 9-12, 13-16
 };
+
+constexpr uint64_t batch_up256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// Byte size of the scratch for n_pairs pairs (one 256-aligned workspace).
+constexpr uint64_t batch_scratch_size(uint64_t n_pairs) {
+  return batch_up256(4 * n_pairs) + batch_up256(16 * n_pairs) + 2 * batch_up256(4 * kKeys) +
+         2 * batch_up256(4 * (kKeys + 1)) + batch_up256(16);
+}
 
 struct BatchArgs {
   FilterArgs f;               // shared fields; f.m is unused (per-read lengths)
@@ -39,8 +47,8 @@ struct BatchArgs {
   BatchScratch s;
 };
 
-// Byte size of the scratch for n_pairs pairs and the layout inside one
-// 256-aligned workspace.
+// batch_scratch_size at run time, and the layout inside one 256-aligned
+// workspace.
 uint64_t batch_scratch_bytes(uint64_t n_pairs);
 BatchScratch batch_scratch_layout(void *base, uint64_t n_pairs);
 
@@ -50,11 +58,53 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
 template <int WPT>
 cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
 
+// Read words 0..W-1 and genome window words off/32 .. off/32 + W of one pair.
+// With a 16-byte aligned read buffer and an even row stride every read row
+// starts on 16 bytes and is read in 16-byte loads (an odd W is below the
+// stride, so the extra word is row padding); otherwise in 8-byte loads.  Window words are read in aligned 16-byte loads from the even
+// word at or below off/32: ceil((W+1)/2) loads, one more when W is odd and
+// off/32 is odd; the last word read is at most n_words + 1, inside the
+// genome's two zero tail words.
+template <int W>
+__device__ __forceinline__ void load_words_wide(const BatchArgs &a, PairData<W> &x) {
+  const uint2 *rp = a.f.reads + (uint64_t)x.rid * a.f.stride_words;
+  if ((a.f.stride_words & 1u) == 0 && (reinterpret_cast<uintptr_t>(a.f.reads) & 15u) == 0) {
+    const uint4 *rq = reinterpret_cast<const uint4 *>(rp);
+#pragma unroll
+    for (int i = 0; i < (W + 1) / 2; ++i) {
+      const uint4 v = rq[i];
+      x.r[2 * i] = make_uint2(v.x, v.y);
+      if (2 * i + 1 < W) x.r[2 * i + 1] = make_uint2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+  }
+  constexpr int NE = (W + 2) / 2;  // ceil((W + 1) / 2)
+  const uint32_t s = x.off >> 5;
+  const bool odd = (s & 1u) != 0;
+  const uint4 *gq = reinterpret_cast<const uint4 *>(a.f.ref_hl + (s & ~1u));
+  uint2 v[2 * NE + 2];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    const uint4 q = gq[i];
+    v[2 * i] = make_uint2(q.x, q.y);
+    v[2 * i + 1] = make_uint2(q.z, q.w);
+  }
+  v[2 * NE] = v[2 * NE + 1] = make_uint2(0u, 0u);
+  if ((W & 1) && odd) {
+    const uint4 q = gq[NE];
+    v[2 * NE] = make_uint2(q.x, q.y);
+  }
+#pragma unroll
+  for (int w = 0; w <= W; ++w) x.g[w] = odd ? v[w + 1] : v[w];
+}
+
 // One pair per lane over a tile of words-per-read W: the plain filter's
 // per-thread code (deferred erosion when the tile's shift count is 3..30
 // with the edge OR on, exact erosion otherwise), each pair with its own m.
 // Every pair of a tile with K <= 30 has e = K; the code clamps the shift
-// count to m - 1 per pair.
+// count to m - 1 per pair.  Records are read in slot order (coalesced).
 template <int W>
 __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t K,
                                            int lane) {
@@ -62,23 +112,18 @@ __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, u
   for (uint32_t base = first; base < end; base += 32) {
     const uint32_t slot = base + (uint32_t)lane;
     if (slot < end) {
-      const uint32_t p = a.s.perm[slot];
+      const uint4 rec = a.s.rec[slot];
       PairData<W> x;
-      x.rid = a.f.pair_read[p];
-      x.off = a.f.pair_off[p];
-      x.e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
-      x.m = a.read_len[x.rid];
+      x.rid = rec.y;
+      x.off = rec.z;
+      x.e = rec.w & 0xFFFFu;
+      x.m = rec.w >> 16;
       x.status = 0;
-      const uint2 *rp = a.f.reads + (uint64_t)x.rid * a.f.stride_words;
-      const uint2 *gp = a.f.ref_hl + (x.off >> 5);
-#pragma unroll
-      for (int w = 0; w < W; ++w) x.r[w] = rp[w];
-#pragma unroll
-      for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+      load_words_wide<W>(a, x);
       const uint32_t count = deferred ? filter_loaded_deferred<W>(a.f, x)
                                       : (K < 32 ? filter_loaded<W, true>(a.f, x) : filter_loaded<W, false>(a.f, x));
-      a.f.accept[p] = count <= x.e;
-      a.f.edits[p] = (uint16_t)count;
+      a.f.accept[rec.x] = count <= x.e;
+      a.f.edits[rec.x] = (uint16_t)count;
     }
   }
 }
@@ -186,11 +231,12 @@ __device__ __forceinline__ void tile_coop(const BatchArgs &a, uint32_t first, ui
 #pragma unroll
       for (int j = 0; j < WPT; ++j) rh[j] = rl[j] = gh[j] = gl[j] = vm[j] = 0;
       if (valid) {
-        p = a.s.perm[slot];
-        const uint32_t rid = a.f.pair_read[p];
-        const uint32_t off = a.f.pair_off[p];
-        e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
-        m = a.read_len[rid];
+        const uint4 rec = a.s.rec[slot];
+        p = rec.x;
+        const uint32_t rid = rec.y;
+        const uint32_t off = rec.z;
+        e = rec.w & 0xFFFFu;
+        m = rec.w >> 16;
         const uint2 *rp = a.f.reads + (uint64_t)rid * a.f.stride_words;
         const uint2 *gp = a.f.ref_hl + (off >> 5);
         const uint32_t sh = off & 31;

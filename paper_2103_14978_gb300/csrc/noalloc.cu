@@ -15,10 +15,8 @@
 namespace {
 
 constexpr uint64_t kNoallocMaxPairs = GK_NOALLOC_MAX_PAIRS;
-constexpr uint64_t up256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 // Same layout as the caller-provided workspace of gk_filter_batched.
-constexpr uint64_t kNoallocBytes = up256(2 * kNoallocMaxPairs) + up256(4 * kNoallocMaxPairs) +
-                                   2 * up256(4 * gk::kKeys) + 2 * up256(4 * (gk::kKeys + 1)) + up256(16);
+constexpr uint64_t kNoallocBytes = gk::batch_scratch_size(kNoallocMaxPairs);
 
 // The scratch itself.  Host code must not use this name as an address: it
 // stands for the host-side shadow; the device address comes from

@@ -143,3 +143,56 @@ def test_autotuner_picks_a_valid_tiling():
     _, got = b.filter_(best)
     sample = np.random.default_rng(2).choice(w.n_pairs, 20000, replace=False)
     assert_same((got[0][sample], got[1][sample]), oracle_run(w, idx=sample), "autotuned")
+
+
+def test_whole_pair_odd_stride_and_unaligned_reads():
+    """One pair per lane with the 8-byte read loads: an odd row stride
+    (9 words for reads up to 288 bases), and an even stride whose read buffer
+    starts 8 bytes past a 16-byte boundary."""
+    w = mixed_workload(34, n_pairs=15000, m=(1, 288))
+    want = oracle_run(w)
+    b = Batched(w)
+    assert b.reads.stride_words == 9
+    for tiling in ((1, 256, 2, 8), (4, 256, 2, 8)):
+        _, got = b.filter_(tiling)
+        assert_same(got, want, f"odd stride {tiling}")
+    r10 = dd.upload_reads(w.reads, w.read_len, w.stride, stride_words=10)
+    buf = torch.zeros(r10.packed.numel() + 2, dtype=torch.int32, device="cuda")
+    buf[2:] = r10.packed
+    shifted = buf[2:]
+    assert shifted.data_ptr() % 16 == 8
+    bf = batch.BatchedFilter(b.ref, shifted, 10, r10.n_reads, b.read_len, r10.nflag, b.pairs.pair_read,
+                             b.pairs.pair_off, b.pairs.pair_e, (1, 256, 2, 8))
+    bf.run()
+    torch.cuda.synchronize()
+    assert_same((bf.accept.cpu().numpy(), dd.edits_u16(bf.edits)), want, "unaligned read buffer")
+
+
+@pytest.mark.parametrize("ref_len", [4096, 4100, 4127])
+def test_batched_windows_at_reference_end(ref_len):
+    """Windows ending at the genome's last base, for W odd and even and
+    window starts in odd and even words (the 16-byte window loads read up to
+    the genome's zero tail words)."""
+    ref = synth.reference(ref_len, 40, 0.0, 0.0)
+    rng = np.random.default_rng(ref_len)
+    ms = np.array([1, 31, 32, 33, 63, 64, 65, 95, 96, 97, 100, 128, 150, 250, 255, 288, 300, 320, 416, 500, 512])
+    rows, lens, offs = [], [], []
+    for m in ms:
+        for o in range(ref_len - int(m) - 70, ref_len - int(m) + 1):
+            seq = np.frombuffer(bytes(ref[o:o + m]), np.uint8).copy()
+            flip = rng.random(m) < 0.03
+            seq[flip] = synth.BASES[rng.integers(0, 4, int(flip.sum()))]
+            row = np.full(512, ord("N"), np.uint8)
+            row[:m] = seq
+            rows.append(row)
+            lens.append(m)
+            offs.append(o)
+    n = len(rows)
+    pair_e = rng.integers(0, 40, n).astype(np.uint8)
+    w = synth.Workload("end-mixed", np.concatenate(rows), np.asarray(lens, np.uint16), 512, ref,
+                       np.arange(n, dtype=np.uint32), np.asarray(offs, np.uint32), pair_e=pair_e)
+    b = Batched(w)
+    want = oracle_run(w)
+    for tiling in ((1, 64, 2, 8), (2, 64, 2, 8)):
+        _, got = b.filter_(tiling)
+        assert_same(got, want, f"end ref_len={ref_len} {tiling}")
