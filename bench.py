@@ -147,9 +147,34 @@ class ClockSampler:
 
 # ---- workload ----------------------------------------------------------------
 
+def shard_seed(rank: int) -> int:
+    """Seed of rank `rank`'s shard: every rank filters its own independent
+    workload of the same size (weak scaling, no data-path collective)."""
+    from paper_2103_14978_gb300 import synth
+    return synth.SEED_BASE + 1 + 1000 * rank
+
+
+def reduce_max(x: float, world: int, device) -> float:
+    """The slowest rank's figure: all-reduce MAX over the ranks (nccl on the
+    GPUs, gloo in the CPU tests); the value itself at world size 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(pairs_per_step: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job Gpairs/s: the pairs every rank filtered in `steps` steps over
+    the slowest rank's time."""
+    return pairs_per_step * world * steps / (max_ms * 1e-3) / 1e9
+
+
 def make_workload(scale: float, rank: int):
     from paper_2103_14978_gb300 import synth
-    return synth.config2(scale=scale, seed=synth.SEED_BASE + 1 + 1000 * rank)
+    return synth.config2(scale=scale, seed=shard_seed(rank))
 
 
 def kernel_source_hash() -> str:
@@ -335,12 +360,9 @@ def run_mine(args):
     elapsed_ms = t_start.elapsed_time(t_end)
     filt_ms = [[evs[k][i][0].elapsed_time(evs[k][i][1]) for i in range(len(E_SWEEP))] for k in range(args.steps)]
 
-    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_max.item())
+    elapsed_ms = reduce_max(elapsed_ms, world, dev)
     pairs_per_step = w.n_pairs * len(E_SWEEP)
-    value = pairs_per_step * world * args.steps / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_rate(pairs_per_step, world, args.steps, elapsed_ms)
 
     # Dominant kernel: the filter.  Algorithmic ops per launch summed over the
     # sweep, divided by the summed CUDA-event durations of those launches.
@@ -432,6 +454,9 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
         step()
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
     s.record(stream)
     for _ in range(steps):
@@ -439,10 +464,10 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
     e.record(stream)
     e.synchronize()
     wall = time.perf_counter() - t0
-    ms = s.elapsed_time(e)
+    ms = reduce_max(s.elapsed_time(e), world, dev)
     h2d = h_asc.numel() + 4 * n * 2
     d2h = len(E_SWEEP) * n * 3
-    return {"value": n * len(E_SWEEP) * steps * world / (ms * 1e-3) / 1e9, "unit": "Gpairs/s",
+    return {"value": whole_job_rate(n * len(E_SWEEP), world, steps, ms), "unit": "Gpairs/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "host_wall_s": wall, "path": "pinned host ASCII reads + pairs -> gk_encode(device) -> "
                                           "11 x gk_filter -> results to pinned host"}
