@@ -58,48 +58,6 @@ cudaError_t launch_batched(int wpt, const BatchArgs &a, uint32_t blocks_per_sm, 
 template <int WPT>
 cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
 
-// Read words 0..W-1 and genome window words off/32 .. off/32 + W of one pair.
-// With a 16-byte aligned read buffer and an even row stride every read row
-// starts on 16 bytes and is read in 16-byte loads (an odd W is below the
-// stride, so the extra word is row padding); otherwise in 8-byte loads.  Window words are read in aligned 16-byte loads from the even
-// word at or below off/32: ceil((W+1)/2) loads, one more when W is odd and
-// off/32 is odd; the last word read is at most n_words + 1, inside the
-// genome's two zero tail words.
-template <int W>
-__device__ __forceinline__ void load_words_wide(const BatchArgs &a, PairData<W> &x) {
-  const uint2 *rp = a.f.reads + (uint64_t)x.rid * a.f.stride_words;
-  if ((a.f.stride_words & 1u) == 0 && (reinterpret_cast<uintptr_t>(a.f.reads) & 15u) == 0) {
-    const uint4 *rq = reinterpret_cast<const uint4 *>(rp);
-#pragma unroll
-    for (int i = 0; i < (W + 1) / 2; ++i) {
-      const uint4 v = rq[i];
-      x.r[2 * i] = make_uint2(v.x, v.y);
-      if (2 * i + 1 < W) x.r[2 * i + 1] = make_uint2(v.z, v.w);
-    }
-  } else {
-#pragma unroll
-    for (int w = 0; w < W; ++w) x.r[w] = rp[w];
-  }
-  constexpr int NE = (W + 2) / 2;  // ceil((W + 1) / 2)
-  const uint32_t s = x.off >> 5;
-  const bool odd = (s & 1u) != 0;
-  const uint4 *gq = reinterpret_cast<const uint4 *>(a.f.ref_hl + (s & ~1u));
-  uint2 v[2 * NE + 2];
-#pragma unroll
-  for (int i = 0; i < NE; ++i) {
-    const uint4 q = gq[i];
-    v[2 * i] = make_uint2(q.x, q.y);
-    v[2 * i + 1] = make_uint2(q.z, q.w);
-  }
-  v[2 * NE] = v[2 * NE + 1] = make_uint2(0u, 0u);
-  if ((W & 1) && odd) {
-    const uint4 q = gq[NE];
-    v[2 * NE] = make_uint2(q.x, q.y);
-  }
-#pragma unroll
-  for (int w = 0; w <= W; ++w) x.g[w] = odd ? v[w + 1] : v[w];
-}
-
 // One pair per lane over a tile of words-per-read W: the plain filter's
 // per-thread code (deferred erosion when the tile's shift count is 3..30
 // with the edge OR on, exact erosion otherwise), each pair with its own m.
@@ -119,7 +77,7 @@ __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, u
       x.e = rec.w & 0xFFFFu;
       x.m = rec.w >> 16;
       x.status = 0;
-      load_words_wide<W>(a, x);
+      load_words_wide<W>(a.f.reads, a.f.stride_words, a.f.ref_hl, x);
       const uint32_t count = deferred ? filter_loaded_deferred<W>(a.f, x)
                                       : (K < 32 ? filter_loaded<W, true>(a.f, x) : filter_loaded<W, false>(a.f, x));
       a.f.accept[rec.x] = count <= x.e;

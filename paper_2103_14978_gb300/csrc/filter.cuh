@@ -69,7 +69,55 @@ struct PairData {
   uint2 g[W + 1]; // reference words covering the window
 };
 
+// Read words 0..W-1 and genome window words off/32 .. off/32 + W of a valid
+// pair (off + m within the genome, W = ceil(m/32) <= the row stride) in
+// 16-byte loads, half the requests of 8-byte loads.  With a 16-byte aligned
+// read buffer and an even row stride every read row starts on 16 bytes (an
+// odd W is below the stride, so the extra word is row padding); otherwise
+// the read takes 8-byte loads.  Window words come in aligned 16-byte loads
+// from the even word at or below off/32: ceil((W+1)/2) loads, one more when
+// W and off/32 are both odd; the last word read is at most n_words + 1,
+// inside the genome's two zero tail words.
 template <int W>
+__device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t stride_words, const uint2 *ref_hl,
+                                                PairData<W> &x) {
+  const uint2 *rp = reads + (uint64_t)x.rid * stride_words;
+  if ((stride_words & 1u) == 0 && (reinterpret_cast<uintptr_t>(reads) & 15u) == 0) {
+    const uint4 *rq = reinterpret_cast<const uint4 *>(rp);
+#pragma unroll
+    for (int i = 0; i < (W + 1) / 2; ++i) {
+      const uint4 v = rq[i];
+      x.r[2 * i] = make_uint2(v.x, v.y);
+      if (2 * i + 1 < W) x.r[2 * i + 1] = make_uint2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+  }
+  constexpr int NE = (W + 2) / 2;  // ceil((W + 1) / 2)
+  const uint32_t s = x.off >> 5;
+  const bool odd = (s & 1u) != 0;
+  const uint4 *gq = reinterpret_cast<const uint4 *>(ref_hl + (s & ~1u));
+  uint2 v[2 * NE + 2];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    const uint4 q = gq[i];
+    v[2 * i] = make_uint2(q.x, q.y);
+    v[2 * i + 1] = make_uint2(q.z, q.w);
+  }
+  v[2 * NE] = v[2 * NE + 1] = make_uint2(0u, 0u);
+  if ((W & 1) && odd) {
+    const uint4 q = gq[NE];
+    v[2 * NE] = make_uint2(q.x, q.y);
+  }
+#pragma unroll
+  for (int w = 0; w <= W; ++w) x.g[w] = odd ? v[w + 1] : v[w];
+}
+
+// Loads pair p.  WIDE: read and window words in 16-byte loads.  The plain
+// kernel keeps 8-byte loads: at e <= 2 (the launches waiting on loads) the
+// wide form measured 2-6% slower at 100 and 150 bp.
+template <int W, bool WIDE = false>
 __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairData<W> &x) {
   x.rid = a.pair_read[p];
   x.off = a.pair_off[p];
@@ -81,12 +129,16 @@ __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairD
   if (x.status == 0 && a.m > 0) {
     if (a.read_nflag) x.nflag = a.read_nflag[x.rid];
     if (a.ref_nidx) x.ni = a.ref_nidx[x.off >> 5];
-    const uint2 *rp = a.reads + (uint64_t)x.rid * a.stride_words;
-    const uint2 *gp = a.ref_hl + (x.off >> 5);
+    if (WIDE) {
+      load_words_wide<W>(a.reads, a.stride_words, a.ref_hl, x);
+    } else {
+      const uint2 *rp = a.reads + (uint64_t)x.rid * a.stride_words;
+      const uint2 *gp = a.ref_hl + (x.off >> 5);
 #pragma unroll
-    for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+      for (int w = 0; w < W; ++w) x.r[w] = rp[w];
 #pragma unroll
-    for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+      for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+    }
   }
 }
 
@@ -335,11 +387,14 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
 
 // Resident blocks per SM the compiler must allow: small reads keep enough
 // registers free for 40 warps per SM, which hides the dependent loads of a
-// pair (ids, then read and window words).
+// pair (ids, then read and window words).  W = 5 and 6 fit 4 and 3 blocks
+// without spilling (at 150 bp, e = 0..2, 4 blocks run 9-18% faster than 2).
 template <int W, bool COMPACT>
 struct MinBlocks {
   static constexpr int value =
-      W <= 2 ? 6 : (W <= 4 ? (COMPACT ? 4 : 5) : (W <= 6 && COMPACT ? 3 : (W <= 8 ? 2 : 1)));
+      W <= 2 ? 6
+             : (W <= 4 ? (COMPACT ? 4 : 5)
+                       : (W == 5 ? (COMPACT ? 3 : 4) : (W == 6 ? 3 : (W <= 8 ? 2 : 1))));
 };
 
 // Status of a loaded pair: 0 filter, 1 undefined (N in read or window),
