@@ -251,6 +251,71 @@ int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
                               uint16_t *edits_out, uint32_t *err_count,
                               void *stream);
 
+/*
+ * Streamed host pipeline.  The paper's host program sends reads and
+ * candidates to the device in batches and reads the results back, with one
+ * synchronisation point per batch (Sec. 3.3, Sec. 3.5).  A pipe keeps
+ * n_slots batches in flight on three streams of its own, so the host-to-
+ * device copy of batch i+1 and the device-to-host copy of batch i-1 overlap
+ * the encoding and filtering of batch i:
+ *   copy in   ASCII reads and pairs (waits until the slot's previous batch
+ *             has been filtered)
+ *   run       gk_encode on the device, then gk_filter once per threshold
+ *             (waits for its copy-in and for the slot's previous copy-out)
+ *   copy out  accept and edit counts of every threshold
+ * Batches hold fixed-length reads (the read length of the pipe).  The pipe
+ * owns its device buffers (n_slots * about max_reads * (ascii_stride +
+ * 8 * ceil(read_len/32) + 1) + max_pairs * (8 + 3 * n_thresholds) bytes),
+ * streams and events, all on the device current at creation; every call
+ * makes that device current and restores the caller's.  One pipe must not
+ * be used from two threads at once.
+ */
+typedef struct gk_pipe_s *gk_pipe_t;
+
+typedef struct {
+  uint64_t max_reads;          /* reads per batch, at most (>= 1) */
+  uint64_t ascii_stride;       /* bytes between read starts in a batch's ASCII, >= read_len */
+  uint32_t read_len;           /* length of every read, 1..GK_MAX_LEN */
+  uint64_t max_pairs;          /* pairs per batch, at most (1 .. 2^32 - 1) */
+  uint32_t n_thresholds;       /* filter passes per batch, 1..64 */
+  const uint8_t *thresholds;   /* host, n_thresholds values of e (copied at creation) */
+  int count_mode;              /* GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT */
+  uint32_t flags;              /* 0 or GK_FLAG_NO_EDGE_FIX */
+  uint32_t n_slots;            /* batches in flight, 2..4 */
+} gk_pipe_desc_t;
+
+/* Create a pipe against a loaded reference (which must outlive it).
+ * Errors: GK_EINVAL (null pointer, a field out of range), GK_ENOMEM,
+ * GK_ECUDA. */
+int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *desc, gk_pipe_t *out);
+
+/*
+ * Enqueue one batch and return at once.
+ *   ascii       host, n_reads * ascii_stride bytes (read i at i*ascii_stride)
+ *   pair_read   host, n_pairs uint32 read ids (within this batch)
+ *   pair_off    host, n_pairs uint32 reference offsets
+ *   accept_out  host, n_thresholds * n_pairs uint8, threshold-major
+ *   edits_out   host, n_thresholds * n_pairs uint16, threshold-major
+ *   ticket      receives the batch's number (0, 1, 2, ... per pipe)
+ * Results are in accept_out / edits_out once gk_pipe_wait(ticket) returns;
+ * all five host buffers must stay valid and unchanged until then.  Copies
+ * overlap other work only from page-locked host memory (cudaHostAlloc or
+ * cudaHostRegister).  Errors: GK_EINVAL / GK_ERANGE (sizes above the pipe's
+ * maxima) before anything is enqueued; GK_ECUDA, after which the pipe only
+ * reports the error.
+ */
+int gk_pipe_submit(gk_pipe_t pipe, const uint8_t *ascii, uint64_t n_reads,
+                   const uint32_t *pair_read, const uint32_t *pair_off,
+                   uint64_t n_pairs, uint8_t *accept_out, uint16_t *edits_out,
+                   uint64_t *ticket);
+
+/* Block until batch `ticket` (and every earlier one) has its results in the
+ * host buffers.  Errors: GK_EINVAL (a ticket not yet submitted), GK_ECUDA. */
+int gk_pipe_wait(gk_pipe_t pipe, uint64_t ticket);
+
+/* Wait for every submitted batch, then release the pipe (NULL is ignored). */
+void gk_pipe_destroy(gk_pipe_t pipe);
+
 #ifdef __cplusplus
 }
 #endif

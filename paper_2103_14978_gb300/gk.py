@@ -26,6 +26,15 @@ _lock = threading.Lock()
 _lib = None
 
 _c = ctypes
+
+
+class PipeDesc(ctypes.Structure):
+    """gk_pipe_desc_t: sizes, read length and thresholds of a streamed pipe."""
+    _fields_ = [("max_reads", ctypes.c_uint64), ("ascii_stride", ctypes.c_uint64), ("read_len", ctypes.c_uint32),
+                ("max_pairs", ctypes.c_uint64), ("n_thresholds", ctypes.c_uint32), ("thresholds", ctypes.c_void_p),
+                ("count_mode", ctypes.c_int), ("flags", ctypes.c_uint32), ("n_slots", ctypes.c_uint32)]
+
+
 _SIGS = {
     "gk_last_error": ([], _c.c_char_p),
     "gk_version": ([], _c.c_int),
@@ -51,6 +60,11 @@ _SIGS = {
     "gk_rebase_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                          _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_copy_many": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_int, _c.c_void_p], _c.c_int),
+    "gk_pipe_create": ([_c.c_void_p, _c.POINTER(PipeDesc), _c.POINTER(_c.c_void_p)], _c.c_int),
+    "gk_pipe_submit": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_uint64,
+                        _c.c_void_p, _c.c_void_p, _c.POINTER(_c.c_uint64)], _c.c_int),
+    "gk_pipe_wait": ([_c.c_void_p, _c.c_uint64], _c.c_int),
+    "gk_pipe_destroy": ([_c.c_void_p], None),
 }
 
 GK_NOALLOC_MAX_PAIRS = 1_000_000
@@ -312,6 +326,80 @@ def gk_copy_many(dst: np.ndarray, src: np.ndarray, nbytes: np.ndarray, kind: int
 
 
 GK_PROBE_LOP3, GK_PROBE_SHF, GK_PROBE_MIX = 0, 1, 2
+
+
+def _hptr(x, dtypes, name: str, numel: int) -> int | None:
+    """Address of a contiguous host buffer (numpy array or CPU tensor) of one
+    of `dtypes` holding at least `numel` elements."""
+    if numel == 0:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or not x.is_contiguous() or x.dtype not in dtypes:
+            raise TypeError(f"{name} must be a contiguous host tensor of {dtypes}")
+        n = x.numel()
+        ptr = x.data_ptr()
+    elif isinstance(x, np.ndarray):  # either signedness of the element width
+        width = torch.empty(0, dtype=dtypes[0]).element_size()
+        if not x.flags.c_contiguous or x.dtype.kind not in "iu" or x.dtype.itemsize != width:
+            raise TypeError(f"{name} must be a contiguous host array of {width}-byte integers")
+        n = x.size
+        ptr = x.ctypes.data
+    else:
+        raise TypeError(f"{name} must be a numpy array or a CPU tensor")
+    if n < numel:
+        raise ValueError(f"{name} holds {n} elements, needs {numel}")
+    return ptr
+
+
+class Pipe:
+    """gk_pipe_*: a streamed host pipeline over fixed-length reads.  Each
+    ``submit`` enqueues one batch (host ASCII reads and pairs in, results of
+    every threshold out, threshold-major) and returns its ticket; ``wait``
+    blocks until that batch's results are in its host buffers.  Host buffers
+    should be page-locked (``tensor.pin_memory()``) for the copies to overlap
+    the filtering; the pipe keeps them referenced until they are waited on."""
+
+    def __init__(self, ref: Reference, max_reads: int, ascii_stride: int, read_len: int, max_pairs: int,
+                 thresholds, count_mode: int = GK_COUNT_RUNS4, flags: int = 0, n_slots: int = 3):
+        th = np.ascontiguousarray(np.asarray(thresholds), dtype=np.uint8)
+        desc = PipeDesc(max_reads, ascii_stride, read_len, max_pairs, th.size, th.ctypes.data, count_mode, flags,
+                        n_slots)
+        h = ctypes.c_void_p()
+        _check(lib().gk_pipe_create(ref.handle, ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h.value
+        self.ref = ref
+        self.ascii_stride = ascii_stride
+        self.n_thresholds = int(th.size)
+        self._held = {}
+
+    def submit(self, ascii, n_reads: int, pair_read, pair_off, accept_out, edits_out) -> int:
+        n_pairs = int(pair_read.shape[0]) if pair_read is not None else 0
+        i32 = (torch.int32,)
+        args = (_hptr(ascii, (torch.uint8,), "ascii", n_reads * self.ascii_stride), n_reads,
+                _hptr(pair_read, i32, "pair_read", n_pairs), _hptr(pair_off, i32, "pair_off", n_pairs), n_pairs,
+                _hptr(accept_out, (torch.uint8,), "accept_out", self.n_thresholds * n_pairs),
+                _hptr(edits_out, (torch.int16,), "edits_out", self.n_thresholds * n_pairs))
+        t = ctypes.c_uint64()
+        _check(lib().gk_pipe_submit(self.handle, *args, ctypes.byref(t)))
+        self._held[t.value] = (ascii, pair_read, pair_off, accept_out, edits_out)
+        return t.value
+
+    def wait(self, ticket: int):
+        _check(lib().gk_pipe_wait(self.handle, ticket))
+        for k in [k for k in self._held if k <= ticket]:
+            del self._held[k]
+
+    def close(self):
+        if self.handle:
+            lib().gk_pipe_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def gk_probe_alu(kind: int, iters: int, blocks: int, threads: int, sink: torch.Tensor, stream=None):

@@ -113,3 +113,14 @@ def test_host_encoder_matches_code_table(libgk):
             w, b = divmod(i, 32)
             assert (packed[(s * sw + w) * 2] >> b) & 1 == 0
             assert (packed[(s * sw + w) * 2 + 1] >> b) & 1 == 0
+
+
+def test_pipe_rejects_bad_arguments_on_host(libgk):
+    L = libgk.lib()
+    h = ctypes.c_void_p()
+    assert L.gk_pipe_create(None, None, ctypes.byref(h)) == libgk.GK_EINVAL
+    assert b"gk_pipe_create" in L.gk_last_error()
+    t = ctypes.c_uint64()
+    assert L.gk_pipe_submit(None, None, 0, None, None, 0, None, None, ctypes.byref(t)) == libgk.GK_EINVAL
+    assert L.gk_pipe_wait(None, 0) == libgk.GK_EINVAL
+    L.gk_pipe_destroy(None)  # ignored
