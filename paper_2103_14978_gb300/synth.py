@@ -258,6 +258,35 @@ def config1(seed: int = SEED_BASE + 0, n_pairs: int = 10_000, m: int = 100, e: i
                     e=e, seed=seed, meta={"edits_per_segment": "U{0..6}", "ref_len": int(ref.shape[0])})
 
 
+def accuracy_set(m: int, k_max: int, n_pairs: int, seed: int = SEED_BASE + 5, unrelated: float = 0.25,
+                 flank: int = 32) -> Workload:
+    """Pairs for the accuracy study: i.i.d. uniform reads of m bases.  A share
+    ``1 - unrelated`` of the segments is the read with k ~ U{0..k_max} random
+    edits (substitution, insertion, deletion with equal odds), so many pairs
+    sit near any threshold; the rest are unrelated random segments.  Each
+    segment is flanked by ``flank`` random bases; the reference is the
+    segments end to end and pair i's offset is segment i's start.
+    ``meta["k"]`` holds the edits applied (-1 for unrelated segments)."""
+    rng = np.random.default_rng([seed, n_pairs, m, k_max, 6])
+    reads = random_bases(rng, n_pairs * m).reshape(n_pairs, m)
+    ext = random_bases(rng, n_pairs * m).reshape(n_pairs, m)
+    text = np.concatenate([reads, ext], axis=1).reshape(-1)
+    starts = np.arange(n_pairs, dtype=np.int64) * (2 * m)
+    k = rng.integers(0, k_max + 1, n_pairs)
+    seg = edited_copies(rng, text, starts, m, k)
+    other = rng.random(n_pairs) < unrelated
+    seg[other] = random_bases(rng, int(other.sum()) * m).reshape(-1, m)
+    k[other] = -1
+    flank_l = random_bases(rng, n_pairs * flank).reshape(n_pairs, flank)
+    flank_r = random_bases(rng, n_pairs * flank).reshape(n_pairs, flank)
+    ref = np.concatenate([flank_l, seg, flank_r], axis=1).reshape(-1)
+    pair_off = (np.arange(n_pairs, dtype=np.int64) * (m + 2 * flank) + flank).astype(np.uint32)
+    return Workload(name=f"accuracy-{m}bp-k{k_max}", reads=reads.reshape(-1).copy(),
+                    read_len=np.full(n_pairs, m, np.uint16), stride=m, ref=ref,
+                    pair_read=np.arange(n_pairs, dtype=np.uint32), pair_off=pair_off, e=0, seed=seed,
+                    meta={"k": k})
+
+
 def config2(scale: float = 1.0, seed: int = SEED_BASE + 1, ref_bases: int = 100_000_000) -> Workload:
     """20M pairs of 100 bp: 5M reads x 4 candidates (the true origin, sampled
     with 0-2% edits, then 3 uniform random offsets) on the 100 Mbp genome.
