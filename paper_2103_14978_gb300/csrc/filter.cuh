@@ -260,26 +260,17 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
   gh[W - 1] &= lastmask;
   gl[W - 1] &= lastmask;
 
-  uint32_t acc[W], d[W];
-  // dilation of d into acc (acc &= dil(d) | z), zeros outside the words
-  auto dil_and = [&](const uint32_t (&dd)[W], int which, uint32_t z0, uint32_t zhi, uint32_t zlo) {
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
-      const uint32_t above = __funnelshift_r(dd[w], w + 1 < W ? dd[w + 1] : 0u, 1);
-      uint32_t z = 0;
-      if (which == 1 && w == 0) z = z0;
-      if (which == 2 && w == W - 1) z = zhi;
-      if (which == 2 && W >= 2 && w == W - 2) z = zlo;
-      acc[w] &= (dd[w] | below | above) | z;
-    }
+  uint32_t acc[W], d[W], dn[W];
+  // dilation of a mask: bit i <- d[i-1] | d[i] | d[i+1], zeros outside the words
+  auto dil = [&](const uint32_t (&dd)[W], int w) -> uint32_t {
+    const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
+    const uint32_t above = __funnelshift_r(dd[w], w + 1 < W ? dd[w + 1] : 0u, 1);
+    return dd[w] | below | above;
   };
 #pragma unroll
-  for (int w = 0; w < W; ++w) {
-    acc[w] = 0xffffffffu;
-    d[w] = (rh[w] ^ gh[w]) | (rl[w] ^ gl[w]);
-  }
-  dil_and(d, 0, 0u, 0u, 0u);  // shift 0
+  for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[w]) | (rl[w] ^ gl[w]);
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[w] = dil(d, w);  // shift 0
 
   const uint32_t K = min(x.e, m - 1);  // <= 30 on this path
   {
@@ -289,9 +280,12 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
       ph[w] = nh[w] = rh[w];
       pl[w] = nl[w] = rl[w];
     }
-    uint32_t lz = 1u;                         // dilated low vacated set: positions 0..k
-    uint32_t tz_hi = ~(lastmask >> 1);        // positions >= m-k-1, top word
-    uint32_t tz_lo = 0u;                      // and the word below it
+    // The vacated positions of each shifted mask are ORed into its difference
+    // vector before the dilation: dil(d | V) = dil(d) | dil(V), the mask ORed
+    // with its dilated vacated set.
+    uint32_t lead = 0u;               // mask +k: positions 0..k-1 (word 0)
+    uint32_t tv_hi = ~lastmask;       // mask -k: positions >= m-k (and >= m), top word
+    uint32_t tv_lo = 0u;              // and the word below it
     for (uint32_t k = 1; k <= K; ++k) {
 #pragma unroll
       for (int w = W - 1; w >= 0; --w) {
@@ -303,16 +297,19 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
         nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
         nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
       }
-      lz = 2u * lz + 1u;
-      tz_lo = __funnelshift_r(tz_lo, tz_hi, 1);
-      tz_hi = (tz_hi >> 1) | 0x80000000u;
+      lead = 2u * lead + 1u;
+      tv_lo = __funnelshift_r(tv_lo, tv_hi, 1);
+      tv_hi = (tv_hi >> 1) | 0x80000000u;
 #pragma unroll
-      for (int w = 0; w < W; ++w) d[w] = (ph[w] ^ gh[w]) | (pl[w] ^ gl[w]);
-      d[W - 1] &= lastmask;
-      dil_and(d, 1, lz, 0u, 0u);
+      for (int w = 0; w < W; ++w) {
+        const uint32_t vp = w == 0 ? lead : 0u;
+        const uint32_t vn = w == W - 1 ? tv_hi : (w == W - 2 ? tv_lo : 0u);
+        d[w] = (ph[w] ^ gh[w]) | vp | (pl[w] ^ gl[w]);
+        dn[w] = (nh[w] ^ gh[w]) | vn | (nl[w] ^ gl[w]);
+      }
+      d[W - 1] &= lastmask;  // the +k copy carries read bases past m
 #pragma unroll
-      for (int w = 0; w < W; ++w) d[w] = (nh[w] ^ gh[w]) | (nl[w] ^ gl[w]);
-      dil_and(d, 2, 0u, tz_hi, tz_lo);
+      for (int w = 0; w < W; ++w) acc[w] &= dil(d, w) & dil(dn, w);
     }
   }
 
@@ -426,11 +423,9 @@ __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p
   a.edits[p] = (uint16_t)count;
 }
 
-// Ids, offset, threshold and N information of pair p only (the status phase
-// of the compacting loop).
-__device__ __forceinline__ int classify_pair(const FilterArgs &a, uint64_t p) {
-  const uint32_t rid = a.pair_read[p];
-  const uint32_t off = a.pair_off[p];
+// Status of a pair from its ids (the classify phase of the compacting loop):
+// 0 filter, 1 undefined, 2 invalid, 3 empty read.
+__device__ __forceinline__ int classify_ids(const FilterArgs &a, uint32_t rid, uint32_t off) {
   if ((uint64_t)rid >= a.n_reads || (uint64_t)off + a.m > a.ref_len) return 2;
   if (a.m == 0) return 3;  // empty read: accept, 0 edits
   if (a.read_nflag && a.read_nflag[rid]) return 1;
@@ -443,14 +438,42 @@ __device__ __forceinline__ int classify_pair(const FilterArgs &a, uint64_t p) {
   return 0;
 }
 
+// 8-byte asynchronous global -> shared copy (bypasses registers) and its
+// group fences.
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kFilterWarps = kFilterThreads / 32;
+
+// Words of one staged batch (32 pairs): W read words and W + 1 window words
+// per pair, stored word-major ([word][lane]) so that lanes touch consecutive
+// 8-byte slots.  Two batches per warp are staged at a time.
+template <int W>
+constexpr int kStageWords = (2 * W + 1) * 32;
+template <int W>
+constexpr size_t compact_smem_bytes() {
+  return (size_t)kFilterWarps * 2 * kStageWords<W> * sizeof(uint2);
+}
+
 // VARIANT 0: any thresholds; 1: every shift count of the launch is < 32;
 // 2: edge OR on and one threshold in 3..30, deferred erosion.
 //
 // COMPACT false: one thread per pair.  COMPACT true (inputs with many
-// undefined pairs): persistent warps take 32 pairs at a time, write the
-// trivial outcomes at once and queue the pairs that need filtering in a
-// 64-slot per-warp shared queue, filtering 32 queued pairs at a time so that
-// no lane idles next to an undefined pair.
+// undefined pairs): persistent warps take 32 pairs at a time (their ids
+// loaded one chunk ahead), write the trivial outcomes at once and queue the
+// pairs that need filtering in a 64-slot per-warp shared queue.  Each full
+// batch of 32 queued pairs has its read and window words copied into shared
+// memory by cp.async while the warp filters the previous batch, so that no
+// lane idles next to an undefined pair and the word loads of one batch hide
+// behind the arithmetic of the other.  Dynamic shared memory:
+// compact_smem_bytes<W>().
 template <int W, int VARIANT, bool COMPACT>
 __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) filter_kernel(const FilterArgs a) {
   if (!COMPACT) {
@@ -472,43 +495,137 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
     filter_and_write<W, VARIANT>(a, p, cur);
     return;
   }
-  __shared__ uint32_t queue[kFilterThreads / 32][64];
+  extern __shared__ uint2 stage_all[];
+  __shared__ uint32_t q_p[kFilterWarps][64], q_rid[kFilterWarps][64], q_off[kFilterWarps][64];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t *q = queue[wib];
+  uint2 *stage = stage_all + wib * 2 * kStageWords<W>;
   const uint64_t n_chunks = (a.n_pairs + 31) / 32;
-  const uint64_t n_warps = (uint64_t)gridDim.x * (kFilterThreads / 32);
-  uint32_t qn = 0;  // warp-uniform queue length
-  for (uint64_t c = blockIdx.x * (uint64_t)(kFilterThreads / 32) + wib;; c += n_warps) {
+  const uint64_t n_warps = (uint64_t)gridDim.x * kFilterWarps;
+  uint64_t c = blockIdx.x * (uint64_t)kFilterWarps + wib;
+  uint32_t next_rid = 0, next_off = 0;  // ids of chunk c, loaded one chunk ahead
+  if (c < n_chunks && c * 32 + lane < a.n_pairs) {
+    next_rid = a.pair_read[c * 32 + lane];
+    next_off = a.pair_off[c * 32 + lane];
+  }
+  uint32_t qn = 0;         // warp-uniform queue length
+  int pend = -1;           // stage buffer of the batch in flight, or none
+  bool pend_has = false;   // this lane holds a pair of that batch
+  uint32_t pend_p = 0, pend_off = 0, pend_e = 0;
+  auto filter_staged = [&]() {
+    if (!pend_has) return;
+    const uint2 *sb = stage + pend * kStageWords<W>;
+    PairData<W> x;
+    x.m = a.m;
+    x.off = pend_off;
+    x.e = pend_e;
+    x.status = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) x.r[w] = sb[w * 32 + lane];
+#pragma unroll
+    for (int w = 0; w <= W; ++w) x.g[w] = sb[(W + w) * 32 + lane];
+    filter_and_write<W, VARIANT>(a, pend_p, x);
+  };
+  for (;; c += n_warps) {
     const bool more = c < n_chunks;
     if (more) {
       const uint64_t p = c * 32 + lane;
       const bool active = p < a.n_pairs;
-      const int status = active ? classify_pair(a, p) : -1;
+      const uint32_t rid = next_rid, off = next_off;
+      const uint64_t c2 = c + n_warps;
+      if (c2 < n_chunks && c2 * 32 + lane < a.n_pairs) {
+        next_rid = a.pair_read[c2 * 32 + lane];
+        next_off = a.pair_off[c2 * 32 + lane];
+      }
+      const int status = active ? classify_ids(a, rid, off) : -1;
       if (a.err_count) {
         const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
         if (bad && lane == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
       }
       if (status > 0) write_trivial(a, p, status == 3 ? 0 : status);
       const unsigned need = __ballot_sync(0xffffffffu, status == 0);
-      if ((need >> lane) & 1u) q[qn + __popc(need & ((1u << lane) - 1u))] = (uint32_t)p;
+      if ((need >> lane) & 1u) {
+        const uint32_t slot = qn + __popc(need & ((1u << lane) - 1u));
+        q_p[wib][slot] = (uint32_t)p;
+        q_rid[wib][slot] = rid;
+        q_off[wib][slot] = off;
+      }
       qn += __popc(need);
       __syncwarp();
     }
     while (qn >= 32 || (!more && qn > 0)) {
       const uint32_t take = qn < 32 ? qn : 32;
       const bool has = (uint32_t)lane < take;
-      const uint32_t pp = has ? q[qn - take + lane] : 0u;
+      const int nb = pend == 0 ? 1 : 0;
+      uint32_t np = 0, noff = 0, ne = a.fixed_e;
+      if (has) {
+        const uint32_t i = qn - take + lane;
+        np = q_p[wib][i];
+        const uint32_t rid = q_rid[wib][i];
+        noff = q_off[wib][i];
+        // a queued pair is valid: its read row holds W words and its window
+        // words off/32 .. off/32 + W lie inside the genome's n_words + 2
+        const uint2 *rp = a.reads + (uint64_t)rid * a.stride_words;
+        const uint2 *gp = a.ref_hl + (noff >> 5);
+        uint2 *sb = stage + nb * kStageWords<W>;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cp_async8(sb + w * 32 + lane, rp + w);
+#pragma unroll
+        for (int w = 0; w <= W; ++w) cp_async8(sb + (W + w) * 32 + lane, gp + w);
+        if (a.pair_e) ne = a.pair_e[np];
+      }
+      cp_async_commit();
       __syncwarp();
       qn -= take;
-      if (has) {
-        PairData<W> cur;
-        load_pair<W>(a, pp, cur);
-        filter_and_write<W, VARIANT>(a, pp, cur);
+      if (pend >= 0) {
+        cp_async_wait<1>();  // the previous batch's copies have landed
+        filter_staged();
       }
-      __syncwarp();
+      pend = nb;
+      pend_has = has;
+      pend_p = np;
+      pend_off = noff;
+      pend_e = ne;
     }
     if (!more) break;
   }
+  if (pend >= 0) {
+    cp_async_wait<0>();
+    filter_staged();
+  }
+}
+
+// Launches one instantiation of the plain filter over a.n_pairs pairs.
+template <int W, int VARIANT>
+cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
+  unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
+  if (!a.compact) {
+    filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+  }
+  // Persistent warps: a few waves of resident blocks.  The dynamic shared
+  // memory limit and the occupancy are set up once per device.
+  constexpr int kMaxDev = 64;
+  static int per_sm[kMaxDev] = {}, sms[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  const size_t smem = compact_smem_bytes<W>();
+  if (per_sm[dev] == 0) {
+    err = cudaFuncSetAttribute(filter_kernel<W, VARIANT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    int n = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, filter_kernel<W, VARIANT, true>, kFilterThreads, smem);
+    if (err != cudaSuccess) return err;
+    per_sm[dev] = n < 1 ? 1 : n;
+  }
+  const uint64_t wave = 4ull * (uint64_t)sms[dev] * (uint64_t)per_sm[dev];
+  if (blocks > wave) blocks = (unsigned)wave;
+  filter_kernel<W, VARIANT, true><<<blocks, kFilterThreads, smem, stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace gk

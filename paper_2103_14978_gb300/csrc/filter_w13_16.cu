@@ -3,40 +3,12 @@
 
 namespace gk {
 
-namespace {
-
-template <int W, int VARIANT>
-cudaError_t launch_one(const FilterArgs &a, cudaStream_t stream) {
-  unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
-  if (a.compact) {  // persistent warps: a few waves of resident blocks
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      const cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel<W, VARIANT, true>,
-                                                                            kFilterThreads, 0);
-      if (err != cudaSuccess) return err;
-      if (per_sm < 1) per_sm = 1;
-    }
-    const uint64_t wave = 4ull * (uint64_t)sms * (uint64_t)per_sm;
-    if (blocks > wave) blocks = (unsigned)wave;
-  }
-  if (a.compact)
-    filter_kernel<W, VARIANT, true><<<blocks, kFilterThreads, 0, stream>>>(a);
-  else
-    filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
 cudaError_t launch_filter_w13_16(int W, int variant, const FilterArgs &a, cudaStream_t stream) {
   switch (W) {
-    case 13: return variant == 2 ? launch_one<13, 2>(a, stream) : variant == 1 ? launch_one<13, 1>(a, stream) : launch_one<13, 0>(a, stream);
-    case 14: return variant == 2 ? launch_one<14, 2>(a, stream) : variant == 1 ? launch_one<14, 1>(a, stream) : launch_one<14, 0>(a, stream);
-    case 15: return variant == 2 ? launch_one<15, 2>(a, stream) : variant == 1 ? launch_one<15, 1>(a, stream) : launch_one<15, 0>(a, stream);
-    case 16: return variant == 2 ? launch_one<16, 2>(a, stream) : variant == 1 ? launch_one<16, 1>(a, stream) : launch_one<16, 0>(a, stream);
+    case 13: return variant == 2 ? launch_filter_variant<13, 2>(a, stream) : variant == 1 ? launch_filter_variant<13, 1>(a, stream) : launch_filter_variant<13, 0>(a, stream);
+    case 14: return variant == 2 ? launch_filter_variant<14, 2>(a, stream) : variant == 1 ? launch_filter_variant<14, 1>(a, stream) : launch_filter_variant<14, 0>(a, stream);
+    case 15: return variant == 2 ? launch_filter_variant<15, 2>(a, stream) : variant == 1 ? launch_filter_variant<15, 1>(a, stream) : launch_filter_variant<15, 0>(a, stream);
+    case 16: return variant == 2 ? launch_filter_variant<16, 2>(a, stream) : variant == 1 ? launch_filter_variant<16, 1>(a, stream) : launch_filter_variant<16, 0>(a, stream);
     default: return cudaErrorInvalidValue;
   }
 }
