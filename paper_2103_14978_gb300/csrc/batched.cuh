@@ -59,14 +59,14 @@ template <int WPT>
 cudaError_t launch_persistent(const BatchArgs &a, uint32_t grid, uint32_t warps_per_block, cudaStream_t stream);
 
 // One pair per lane over a tile of words-per-read W: the plain filter's
-// per-thread code (deferred erosion when the tile's shift count is 3..30
+// per-thread code (deferred erosion when the tile's shift count is 2..30
 // with the edge OR on, exact erosion otherwise), each pair with its own m.
 // Every pair of a tile with K <= 30 has e = K; the code clamps the shift
 // count to m - 1 per pair.  Records are read in slot order (coalesced).
 template <int W>
 __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, uint32_t end, uint32_t K,
                                            int lane) {
-  const bool deferred = a.f.edge_on && K >= 3 && K <= 30;
+  const bool deferred = a.f.edge_on && K >= 2 && K <= 30;
   for (uint32_t base = first; base < end; base += 32) {
     const uint32_t slot = base + (uint32_t)lane;
     if (slot < end) {

@@ -382,16 +382,17 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
   return count;
 }
 
-// Resident blocks per SM the compiler must allow: small reads keep enough
-// registers free for 40 warps per SM, which hides the dependent loads of a
-// pair (ids, then read and window words).  W = 5 and 6 fit 4 and 3 blocks
-// without spilling (at 150 bp, e = 0..2, 4 blocks run 9-18% faster than 2).
+// Resident blocks per SM the compiler must allow.  One thread per pair:
+// small reads keep enough registers free for 40 warps per SM, which hides
+// the dependent loads of a pair (ids, then read and window words); W = 5 and
+// 6 fit 4 and 3 blocks without spilling (at 150 bp, e = 0..2, 4 blocks run
+// 9-18% faster than 2).  The compacting loop stages its words with cp.async
+// and carries a chunk pipeline, so it keeps fewer resident warps.
 template <int W, bool COMPACT>
 struct MinBlocks {
   static constexpr int value =
-      W <= 2 ? 6
-             : (W <= 4 ? (COMPACT ? 4 : 5)
-                       : (W == 5 ? (COMPACT ? 3 : 4) : (W == 6 ? 3 : (W <= 8 ? 2 : 1))));
+      COMPACT ? (W <= 2 ? 5 : (W <= 4 ? 4 : (W <= 6 ? 3 : (W <= 8 ? 2 : 1))))
+              : (W <= 2 ? 6 : (W <= 4 ? 5 : (W == 5 ? 4 : (W == 6 ? 3 : (W <= 8 ? 2 : 1)))));
 };
 
 // Status of a loaded pair: 0 filter, 1 undefined (N in read or window),
@@ -423,19 +424,50 @@ __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p
   a.edits[p] = (uint16_t)count;
 }
 
-// Status of a pair from its ids (the classify phase of the compacting loop):
-// 0 filter, 1 undefined, 2 invalid, 3 empty read.
-__device__ __forceinline__ int classify_ids(const FilterArgs &a, uint32_t rid, uint32_t off) {
-  if ((uint64_t)rid >= a.n_reads || (uint64_t)off + a.m > a.ref_len) return 2;
-  if (a.m == 0) return 3;  // empty read: accept, 0 edits
-  if (a.read_nflag && a.read_nflag[rid]) return 1;
-  if (a.ref_nidx) {
-    const uint2 ni = a.ref_nidx[off >> 5];
-    const uint32_t q = ni.x >> (off & 31);
-    const uint64_t first = q ? (uint64_t)off + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
-    if (first < (uint64_t)off + a.m) return 1;
+// The classify phase of the compacting loop, in two steps so that the loads
+// of one chunk are in flight while the warp works on another.
+// ChunkLoads holds one lane's pair of a chunk: its ids and, for a valid pair,
+// the read's N flag and the N index word of its window (loaded together).
+struct ChunkLoads {
+  uint32_t rid, off;
+  uint32_t nflag;
+  uint2 ni;
+  int state;  // -1 no pair, 2 invalid, 3 empty read, 0 defined unless N
+};
+
+__device__ __forceinline__ void chunk_issue(const FilterArgs &a, ChunkLoads &x) {
+  x.nflag = 0;
+  x.ni = make_uint2(0u, 0xffffffffu);
+  if (x.state < 0) return;
+  if ((uint64_t)x.rid >= a.n_reads || (uint64_t)x.off + a.m > a.ref_len) {
+    x.state = 2;
+  } else if (a.m == 0) {
+    x.state = 3;
+  } else {
+    x.state = 0;
+    if (a.read_nflag) x.nflag = a.read_nflag[x.rid];
+    if (a.ref_nidx) x.ni = a.ref_nidx[x.off >> 5];
   }
-  return 0;
+}
+
+// 0 filter, 1 undefined, 2 invalid, 3 empty read, -1 no pair.
+__device__ __forceinline__ int chunk_status(const FilterArgs &a, const ChunkLoads &x) {
+  if (x.state != 0) return x.state;
+  if (x.nflag) return 1;
+  const uint32_t q = x.ni.x >> (x.off & 31);
+  const uint64_t first = q ? (uint64_t)x.off + (uint32_t)(__ffs(q) - 1) : (uint64_t)x.ni.y;
+  return first < (uint64_t)x.off + a.m ? 1 : 0;
+}
+
+__device__ __forceinline__ void chunk_ids(const FilterArgs &a, uint64_t c, uint64_t n_chunks, int lane,
+                                          uint32_t &rid, uint32_t &off, int &state) {
+  const uint64_t p = c * 32 + lane;
+  state = -1;
+  if (c < n_chunks && p < a.n_pairs) {
+    rid = a.pair_read[p];
+    off = a.pair_off[p];
+    state = 0;
+  }
 }
 
 // 8-byte asynchronous global -> shared copy (bypasses registers) and its
@@ -463,7 +495,7 @@ constexpr size_t compact_smem_bytes() {
 }
 
 // VARIANT 0: any thresholds; 1: every shift count of the launch is < 32;
-// 2: edge OR on and one threshold in 3..30, deferred erosion.
+// 2: edge OR on and one threshold in 2..30, deferred erosion.
 //
 // COMPACT false: one thread per pair.  COMPACT true (inputs with many
 // undefined pairs): persistent warps take 32 pairs at a time (their ids
@@ -502,10 +534,20 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
   const uint64_t n_chunks = (a.n_pairs + 31) / 32;
   const uint64_t n_warps = (uint64_t)gridDim.x * kFilterWarps;
   uint64_t c = blockIdx.x * (uint64_t)kFilterWarps + wib;
-  uint32_t next_rid = 0, next_off = 0;  // ids of chunk c, loaded one chunk ahead
-  if (c < n_chunks && c * 32 + lane < a.n_pairs) {
-    next_rid = a.pair_read[c * 32 + lane];
-    next_off = a.pair_off[c * 32 + lane];
+  // Load pipeline over this warp's chunks.  Wide reads (W >= 7, registers to
+  // spare) run it two deep: while the warp classifies chunk c and filters,
+  // the N information of its next chunk and the ids of the chunk after are
+  // in flight.  Narrower reads keep one deep (the ids of the next chunk), as
+  // two deep spills registers there and measured slower at 150 bp.
+  constexpr bool kDeep = W >= 7;
+  ChunkLoads cur;
+  cur.rid = cur.off = 0;
+  chunk_ids(a, c, n_chunks, lane, cur.rid, cur.off, cur.state);
+  uint32_t next_rid = 0, next_off = 0;
+  int next_state = -1;
+  if (kDeep) {
+    chunk_issue(a, cur);
+    chunk_ids(a, c + n_warps, n_chunks, lane, next_rid, next_off, next_state);
   }
   uint32_t qn = 0;         // warp-uniform queue length
   int pend = -1;           // stage buffer of the batch in flight, or none
@@ -530,18 +572,26 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
     if (more) {
       const uint64_t p = c * 32 + lane;
       const bool active = p < a.n_pairs;
-      const uint32_t rid = next_rid, off = next_off;
-      const uint64_t c2 = c + n_warps;
-      if (c2 < n_chunks && c2 * 32 + lane < a.n_pairs) {
-        next_rid = a.pair_read[c2 * 32 + lane];
-        next_off = a.pair_off[c2 * 32 + lane];
+      int status;
+      const uint32_t rid = cur.rid, off = cur.off;
+      if (kDeep) {
+        status = chunk_status(a, cur);
+        cur.rid = next_rid;
+        cur.off = next_off;
+        cur.state = next_state;
+        chunk_issue(a, cur);
+        chunk_ids(a, c + 2 * n_warps, n_chunks, lane, next_rid, next_off, next_state);
+      } else {
+        ChunkLoads x = cur;
+        chunk_ids(a, c + n_warps, n_chunks, lane, cur.rid, cur.off, cur.state);
+        chunk_issue(a, x);
+        status = chunk_status(a, x);
       }
-      const int status = active ? classify_ids(a, rid, off) : -1;
       if (a.err_count) {
         const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
         if (bad && lane == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
       }
-      if (status > 0) write_trivial(a, p, status == 3 ? 0 : status);
+      if (status > 0 && active) write_trivial(a, p, status == 3 ? 0 : status);
       const unsigned need = __ballot_sync(0xffffffffu, status == 0);
       if ((need >> lane) & 1u) {
         const uint32_t slot = qn + __popc(need & ((1u << lane) - 1u));
@@ -598,18 +648,18 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
 template <int W, int VARIANT>
 cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
   unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
-  if (!a.compact) {
+  if (a.compact == 0) {
     filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
     return cudaGetLastError();
   }
   // Persistent warps: a few waves of resident blocks.  The dynamic shared
   // memory limit and the occupancy are set up once per device.
   constexpr int kMaxDev = 64;
-  static int per_sm[kMaxDev] = {}, sms[kMaxDev] = {};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  static int per_sm[kMaxDev] = {}, sms[kMaxDev] = {};
   const size_t smem = compact_smem_bytes<W>();
   if (per_sm[dev] == 0) {
     err = cudaFuncSetAttribute(filter_kernel<W, VARIANT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -39,8 +39,9 @@ cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
   // 32 bases): the edge vectors live in the end words only.
   const bool small = (!a.pair_e && a.fixed_e < 32) || a.m <= 32;
   // Deferred erosion: every shift count <= 30, edge OR on, and enough shifts
-  // (e >= 3) to repay its once-per-pair corrections.
-  const bool deferred = a.edge_on && !a.pair_e && a.fixed_e >= 3 && (a.fixed_e <= 30 || a.m <= 31);
+  // (e >= 2) to repay its once-per-pair corrections (measured on GB300: from
+  // e = 2 it is as fast or faster at 100-300 bp).
+  const bool deferred = a.edge_on && !a.pair_e && a.fixed_e >= 2 && (a.fixed_e <= 30 || a.m <= 31);
   const int variant = deferred ? 2 : (small ? 1 : 0);
   if (W >= 1 && W <= 4) return launch_filter_w1_4(W, variant, a, stream);
   if (W <= 8) return launch_filter_w5_8(W, variant, a, stream);
@@ -242,10 +243,18 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.accept = accept_out;
   a.edits = edits_out;
   a.err_count = err_count;
-  // A genome with N makes a large share of windows undefined (0.1% N gives
-  // 1 - 0.999^m of them): filter only the defined pairs, in full warps, when
-  // the per-pair work (e >= 3, or per-pair thresholds) repays the queueing.
-  a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 && (pair_e || fixed_e >= 3)) ? 1 : 0;
+  // A genome with N makes a share of windows undefined (about 1 - (1-r)^m
+  // for an N density r): filter only the defined pairs, in full warps, when
+  // that share (r*m >= 0.05) and the per-pair work repay the queueing.  The
+  // thresholds are GB300 measurements on 10M pairs at 0.1% N in genome and
+  // reads: the queue wins from e >= 1 at W >= 7 (200-300 bp), from e >= 3 at
+  // W = 5 (150 bp) and from e >= 7 at W = 4 (100 bp); below them one thread
+  // per pair is faster, its loads issued together.  Per-pair thresholds
+  // always queue.
+  const uint32_t e_queue = W >= 7 ? 1u : (W >= 5 ? 3u : 7u);
+  const bool n_dense = (double)ref->n_undefined * (double)m >= 0.05 * (double)ref->n_bases;
+  a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 &&
+               (pair_e || (n_dense && fixed_e >= e_queue))) ? 1 : 0;
   return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
 }
 

@@ -76,11 +76,30 @@ def test_undefined_bases():
         ref[o if i % 2 == 0 else o + 149] = ord("N")
     w.ref = ref
     run = GpuRun(w)
-    for e in (0, 4, 15):
+    for e in (0, 2, 4, 8, 15):
         got = run.filter(e=e)
         assert_same(got, oracle_run(w, e), f"N e={e}")
     assert (got[1] == gk.GK_EDITS_UNDEFINED).sum() > 300
     assert run.ref.n_undefined == int((ref == ord("N")).sum())
+
+
+@pytest.mark.parametrize("m", [64, 100, 180, 200, 250, 300])
+def test_undefined_bases_both_layouts(m):
+    """A genome and reads with N: thresholds on both sides of the switch
+    between one thread per pair and the queue of defined pairs, per-pair
+    thresholds, and invalid pairs counted on either side."""
+    w = small_workload(m, 6000, seed=900 + m, n_frac=0.001, read_n_frac=0.001, cands=(8, 64),
+                       e_rates=(0.0, 0.02, 0.05, 0.10))
+    rng = np.random.default_rng(m)
+    bad = rng.choice(w.n_pairs, 40, replace=False)
+    w.pair_read[bad[:20]] = w.n_reads + 3
+    w.pair_off[bad[20:]] = w.ref.shape[0] - m + 1
+    run = GpuRun(w)
+    for e in (0, 1, 2, 3, 4, 6, 7, 9, 10, 12):
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        assert_same(run.filter(e=e, err=err), oracle_run(w, e), f"N m={m} e={e}")
+        assert int(err.item()) == 40
+    assert_same(run.filter(), oracle_run(w), f"N m={m} per-pair e")
 
 
 def test_invalid_pairs_and_error_counter():
@@ -176,13 +195,13 @@ def test_config3_structure_scaled(m, es):
 
 
 @pytest.mark.parametrize("m", [2, 3, 4, 31, 32, 33, 64, 95, 96, 97, 100, 128, 150, 250, 256, 300])
-def test_every_threshold_3_to_30(m):
-    """One launch per threshold e = 3..30 (the launches whose masks are ANDed
+def test_every_threshold_2_to_30(m):
+    """One launch per threshold e = 2..30 (the launches whose masks are ANDed
     dilated and eroded once, with end corrections), word-boundary lengths
     included, against the oracle; also with N in reads and genome."""
     w = small_workload(m, 1200, seed=300 + m, n_frac=0.0005, read_n_frac=0.0005)
     run = GpuRun(w)
-    for e in range(3, 31):
+    for e in range(2, 31):
         assert_same(run.filter(e=e), oracle_run(w, e), f"m={m} e={e}")
     for e in (4, 17, 30):
         assert_same(run.filter(e=e, mode=gk.GK_COUNT_POPCOUNT), oracle_run(w, e, O.POPCOUNT),
