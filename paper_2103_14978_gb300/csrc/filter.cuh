@@ -240,27 +240,19 @@ __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const Pai
 // the window and on which window bases are 'A', so their corrections for all
 // k are computed once per pair; so are the two values of the AND one base
 // outside each end that the final erosion reads.
-template <int W>
-__device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, const PairData<W> &x) {
-  const uint32_t m = x.m;
+// Deferred-erosion counts of NP pairs that share one read and one shift
+// count K, each against its own window: the read's +k and -k copies (4W
+// funnel shifts per step) are built once for all NP windows.  rh/rl and
+// gh/gl are the read's and the windows' planes, zero past m.
+template <int W, int NP>
+__device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m, uint32_t K,
+                                                const uint32_t (&rh)[W], const uint32_t (&rl)[W],
+                                                const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
+                                                uint32_t (&count)[NP]) {
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 
-  uint32_t rh[W], rl[W], gh[W], gl[W];
-  const uint32_t sh = x.off & 31;
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    rh[w] = x.r[w].x;
-    rl[w] = x.r[w].y;
-    gh[w] = __funnelshift_r(x.g[w].x, x.g[w + 1].x, sh);
-    gl[w] = __funnelshift_r(x.g[w].y, x.g[w + 1].y, sh);
-  }
-  rh[W - 1] &= lastmask;
-  rl[W - 1] &= lastmask;
-  gh[W - 1] &= lastmask;
-  gl[W - 1] &= lastmask;
-
-  uint32_t acc[W], d[W], dn[W];
+  uint32_t acc[NP][W], d[W], dn[W];
   // dilation of a mask: bit i <- d[i-1] | d[i] | d[i+1], zeros outside the words
   auto dil = [&](const uint32_t (&dd)[W], int w) -> uint32_t {
     const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
@@ -268,11 +260,12 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
     return dd[w] | below | above;
   };
 #pragma unroll
-  for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[w]) | (rl[w] ^ gl[w]);
+  for (int j = 0; j < NP; ++j) {
 #pragma unroll
-  for (int w = 0; w < W; ++w) acc[w] = dil(d, w);  // shift 0
-
-  const uint32_t K = min(x.e, m - 1);  // <= 30 on this path
+    for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[j][w]) | (rl[w] ^ gl[j][w]);
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[j][w] = dil(d, w);  // shift 0
+  }
   {
     uint32_t ph[W], pl[W], nh[W], nl[W];
 #pragma unroll
@@ -299,87 +292,121 @@ __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, 
       }
       lead = 2u * lead + 1u;
       tv_lo = __funnelshift_r(tv_lo, tv_hi, 1);
-      tv_hi = (tv_hi >> 1) | 0x80000000u;
+      tv_hi = __funnelshift_r(tv_hi, 0xffffffffu, 1);
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const uint32_t vp = w == 0 ? lead : 0u;
-        const uint32_t vn = w == W - 1 ? tv_hi : (w == W - 2 ? tv_lo : 0u);
-        d[w] = (ph[w] ^ gh[w]) | vp | (pl[w] ^ gl[w]);
-        dn[w] = (nh[w] ^ gh[w]) | vn | (nl[w] ^ gl[w]);
+      for (int j = 0; j < NP; ++j) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const uint32_t vp = w == 0 ? lead : 0u;
+          const uint32_t vn = w == W - 1 ? tv_hi : (w == W - 2 ? tv_lo : 0u);
+          d[w] = (ph[w] ^ gh[j][w]) | vp | (pl[w] ^ gl[j][w]);
+          dn[w] = (nh[w] ^ gh[j][w]) | vn | (nl[w] ^ gl[j][w]);
+        }
+        d[W - 1] &= lastmask;  // the +k copy carries read bases past m
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j][w] &= dil(d, w) & dil(dn, w);
       }
-      d[W - 1] &= lastmask;  // the +k copy carries read bases past m
-#pragma unroll
-      for (int w = 0; w < W; ++w) acc[w] &= dil(d, w) & dil(dn, w);
     }
   }
 
   // ---- once per pair: end values of the AND, corrections, final erosion ----
   const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
-  // AND one base below position 0: every non-positive shift compares G[0]
-  // with R[j], j = 0..K.
-  const uint32_t g0h = 0u - (gh[0] & 1u), g0l = 0u - (gl[0] & 1u);
-  const uint32_t q0 = (rh[0] ^ g0h) | (rl[0] ^ g0l);
-  const uint32_t vlo = ((~q0 & rangeK) == 0) ? 1u : 0u;
-  // Top two words as 64-bit windows; bit b is position 32(W-2) + b.
-  const uint64_t GH = ((uint64_t)gh[W - 1] << 32) | (W >= 2 ? gh[W >= 2 ? W - 2 : 0] : 0u);
-  const uint64_t GL = ((uint64_t)gl[W - 1] << 32) | (W >= 2 ? gl[W >= 2 ? W - 2 : 0] : 0u);
   const uint64_t RH = ((uint64_t)rh[W - 1] << 32) | (W >= 2 ? rh[W >= 2 ? W - 2 : 0] : 0u);
   const uint64_t RL = ((uint64_t)rl[W - 1] << 32) | (W >= 2 ? rl[W >= 2 ? W - 2 : 0] : 0u);
   const uint32_t tpos = tail + 32u;  // bit of position m in the 64-bit windows
-  // AND one base above position m-1, needed only when m fills the words:
-  // every non-negative shift compares G[m-1] with R[m-1-j], j = 0..K.
-  uint32_t vtop = 0u;
-  if (tail == 32) {
-    const uint64_t gmh = 0ull - ((GH >> (tpos - 1)) & 1ull), gml = 0ull - ((GL >> (tpos - 1)) & 1ull);
-    const uint64_t qm = (RH ^ gmh) | (RL ^ gml);
-    const uint64_t rng = (((uint64_t)rangeK) << (tpos - 1 - K));
-    vtop = ((~qm & rng) == 0) ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    // AND one base below position 0: every non-positive shift compares G[0]
+    // with R[i], i = 0..K.
+    const uint32_t g0h = 0u - (gh[j][0] & 1u), g0l = 0u - (gl[j][0] & 1u);
+    const uint32_t q0 = (rh[0] ^ g0h) | (rl[0] ^ g0l);
+    const uint32_t vlo = ((~q0 & rangeK) == 0) ? 1u : 0u;
+    // Top two words as 64-bit windows; bit b is position 32(W-2) + b.
+    const uint64_t GH = ((uint64_t)gh[j][W - 1] << 32) | (W >= 2 ? gh[j][W >= 2 ? W - 2 : 0] : 0u);
+    const uint64_t GL = ((uint64_t)gl[j][W - 1] << 32) | (W >= 2 ? gl[j][W >= 2 ? W - 2 : 0] : 0u);
+    // AND one base above position m-1, needed only when m fills the words:
+    // every non-negative shift compares G[m-1] with R[m-1-i], i = 0..K.
+    uint32_t vtop = 0u;
+    if (tail == 32) {
+      const uint64_t gmh = 0ull - ((GH >> (tpos - 1)) & 1ull), gml = 0ull - ((GL >> (tpos - 1)) & 1ull);
+      const uint64_t qm = (RH ^ gmh) | (RL ^ gml);
+      const uint64_t rng = (((uint64_t)rangeK) << (tpos - 1 - K));
+      vtop = ((~qm & rng) == 0) ? 1u : 0u;
+    }
+    uint32_t f[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t lo_in = w > 0 ? acc[j][w - 1] : (vlo << 31);
+      const uint32_t hi_in = w + 1 < W ? acc[j][w + 1] : vtop;
+      f[w] = acc[j][w] & __funnelshift_l(lo_in, acc[j][w], 1) & __funnelshift_r(acc[j][w], hi_in, 1);
+    }
+    // Low-end corrections (positions 1..K+1, word 0).
+    {
+      const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);
+      const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);
+      const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
+      const uint32_t a0 = (gh[j][0] ^ r0h) | (gl[j][0] ^ r0l);
+      const uint32_t a1 = ((gh[j][0] ^ r1h) | (gl[j][0] ^ r1l)) & v0;
+      const uint32_t vac = gh[j][0] | gl[j][0];
+      const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
+      const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
+      const uint32_t r1k = rangeK & ~1u;
+      f[0] &= ~((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));
+    }
+    // High-end corrections (positions m-K-2..m-2, top two words).
+    {
+      const uint64_t b0h = 0ull - ((RH >> (tpos - 1)) & 1ull), b0l = 0ull - ((RL >> (tpos - 1)) & 1ull);
+      const uint64_t b1h = 0ull - ((RH >> (tpos - 2)) & 1ull), b1l = 0ull - ((RL >> (tpos - 2)) & 1ull);
+      const uint64_t B0 = (GH ^ b0h) | (GL ^ b0l);
+      const uint64_t B1 = (GH ^ b1h) | (GL ^ b1l);
+      const uint64_t vac = GH | GL;
+      const uint64_t e1 = (B1 << 1) | B0 | (vac >> 1);
+      const uint64_t e2 = B0 | (vac >> 1) | (vac >> 2);
+      const uint64_t rh_range = ((1ull << (tpos - 1)) - 1ull) & ~((1ull << (tpos - K - 1)) - 1ull);
+      const uint64_t nc = (~(e1 & e2) & rh_range) | ((~e1 & rh_range) >> 1);
+      f[W - 1] &= ~(uint32_t)(nc >> 32);
+      if (W >= 2) f[W >= 2 ? W - 2 : 0] &= ~(uint32_t)nc;
+    }
+    f[W - 1] &= lastmask;
+
+    uint32_t c = 0;
+    if (a.count_mode == GK_COUNT_POPCOUNT) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) c += __popc(f[w]);
+    } else {
+#pragma unroll
+      for (int w = 0; w < W; ++w) c += __popc(f[w] & ~((f[w] << 1) & 0xEEEEEEEEu));
+    }
+    count[j] = c;
   }
-  uint32_t f[W];
+}
+
+// Read and window planes of a loaded pair, zero past m.
+template <int W>
+__device__ __forceinline__ void pair_planes(const PairData<W> &x, uint32_t (&rh)[W], uint32_t (&rl)[W],
+                                            uint32_t (&gh)[W], uint32_t (&gl)[W]) {
+  const uint32_t tail = x.m - 32u * (W - 1);
+  const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
+  const uint32_t sh = x.off & 31;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    const uint32_t lo_in = w > 0 ? acc[w - 1] : (vlo << 31);
-    const uint32_t hi_in = w + 1 < W ? acc[w + 1] : vtop;
-    f[w] = acc[w] & __funnelshift_l(lo_in, acc[w], 1) & __funnelshift_r(acc[w], hi_in, 1);
+    rh[w] = x.r[w].x;
+    rl[w] = x.r[w].y;
+    gh[w] = __funnelshift_r(x.g[w].x, x.g[w + 1].x, sh);
+    gl[w] = __funnelshift_r(x.g[w].y, x.g[w + 1].y, sh);
   }
-  // Low-end corrections (positions 1..K+1, word 0).
-  {
-    const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);
-    const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);
-    const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
-    const uint32_t a0 = (gh[0] ^ r0h) | (gl[0] ^ r0l);
-    const uint32_t a1 = ((gh[0] ^ r1h) | (gl[0] ^ r1l)) & v0;
-    const uint32_t vac = gh[0] | gl[0];
-    const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
-    const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
-    const uint32_t r1k = rangeK & ~1u;
-    f[0] &= ~((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));
-  }
-  // High-end corrections (positions m-K-2..m-2, top two words).
-  {
-    const uint64_t b0h = 0ull - ((RH >> (tpos - 1)) & 1ull), b0l = 0ull - ((RL >> (tpos - 1)) & 1ull);
-    const uint64_t b1h = 0ull - ((RH >> (tpos - 2)) & 1ull), b1l = 0ull - ((RL >> (tpos - 2)) & 1ull);
-    const uint64_t B0 = (GH ^ b0h) | (GL ^ b0l);
-    const uint64_t B1 = (GH ^ b1h) | (GL ^ b1l);
-    const uint64_t vac = GH | GL;
-    const uint64_t e1 = (B1 << 1) | B0 | (vac >> 1);
-    const uint64_t e2 = B0 | (vac >> 1) | (vac >> 2);
-    const uint64_t rh_range = ((1ull << (tpos - 1)) - 1ull) & ~((1ull << (tpos - K - 1)) - 1ull);
-    const uint64_t nc = (~(e1 & e2) & rh_range) | ((~e1 & rh_range) >> 1);
-    f[W - 1] &= ~(uint32_t)(nc >> 32);
-    if (W >= 2) f[W >= 2 ? W - 2 : 0] &= ~(uint32_t)nc;
-  }
-  f[W - 1] &= lastmask;
+  rh[W - 1] &= lastmask;
+  rl[W - 1] &= lastmask;
+  gh[W - 1] &= lastmask;
+  gl[W - 1] &= lastmask;
+}
 
-  uint32_t count = 0;
-  if (a.count_mode == GK_COUNT_POPCOUNT) {
-#pragma unroll
-    for (int w = 0; w < W; ++w) count += __popc(f[w]);
-  } else {
-#pragma unroll
-    for (int w = 0; w < W; ++w) count += __popc(f[w] & ~((f[w] << 1) & 0xEEEEEEEEu));
-  }
-  return count;
+template <int W>
+__device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, const PairData<W> &x) {
+  uint32_t rh[W], rl[W], gh[1][W], gl[1][W], count[1];
+  pair_planes<W>(x, rh, rl, gh[0], gl[0]);
+  deferred_counts<W, 1>(a, x.m, min(x.e, x.m - 1), rh, rl, gh, gl, count);
+  return count[0];
 }
 
 // Resident blocks per SM the compiler must allow.  One thread per pair:
@@ -644,11 +671,76 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
   }
 }
 
+// Resident blocks per SM of the two-pairs-per-thread kernel.
+template <int W>
+struct MinBlocks2 {
+  static constexpr int value = W <= 2 ? 4 : 3;
+};
+
+// Deferred erosion (VARIANT 2), two pairs per thread: pairs 2t and 2t+1.
+// When both are filtered and share their read (the candidates of one read
+// usually sit next to each other), the read's shifted copies serve both
+// windows: a shift step costs about 13W integer operations per pair instead
+// of 15W.  Otherwise each pair is filtered on its own.
+template <int W>
+__global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_pair2_kernel(const FilterArgs a) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t p0 = 2 * t, p1 = p0 + 1;
+  const bool act0 = p0 < a.n_pairs, act1 = p1 < a.n_pairs;
+  PairData<W> x0, x1;
+  x0.status = x1.status = 0;
+  if (act0) load_pair<W>(a, p0, x0);
+  if (act1) load_pair<W>(a, p1, x1);
+  if (a.err_count) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, act0 && x0.status == 2);
+    const unsigned b1 = __ballot_sync(0xffffffffu, act1 && x1.status == 2);
+    if ((b0 | b1) && (threadIdx.x & 31) == 0) atomicAdd(a.err_count, (unsigned)(__popc(b0) + __popc(b1)));
+  }
+  const int s0 = act0 ? pair_status<W>(a, x0) : -1;
+  const int s1 = act1 ? pair_status<W>(a, x1) : -1;
+  if (s0 > 0) write_trivial(a, p0, s0);
+  if (s1 > 0) write_trivial(a, p1, s1);
+  if (s0 == 0 && s1 == 0 && x0.rid == x1.rid) {
+    uint32_t rh[W], rl[W], gh[2][W], gl[2][W], count[2];
+    pair_planes<W>(x0, rh, rl, gh[0], gl[0]);
+    {
+      const uint32_t tail = a.m - 32u * (W - 1);
+      const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
+      const uint32_t sh = x1.off & 31;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        gh[1][w] = __funnelshift_r(x1.g[w].x, x1.g[w + 1].x, sh);
+        gl[1][w] = __funnelshift_r(x1.g[w].y, x1.g[w + 1].y, sh);
+      }
+      gh[1][W - 1] &= lastmask;
+      gl[1][W - 1] &= lastmask;
+    }
+    deferred_counts<W, 2>(a, a.m, min(a.fixed_e, a.m - 1), rh, rl, gh, gl, count);
+    a.accept[p0] = count[0] <= a.fixed_e;
+    a.edits[p0] = (uint16_t)count[0];
+    a.accept[p1] = count[1] <= a.fixed_e;
+    a.edits[p1] = (uint16_t)count[1];
+  } else {
+    if (s0 == 0) filter_and_write<W, 2>(a, p0, x0);
+    if (s1 == 0) filter_and_write<W, 2>(a, p1, x1);
+  }
+}
+
 // Launches one instantiation of the plain filter over a.n_pairs pairs.
 template <int W, int VARIANT>
 cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
   unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
   if (a.compact == 0) {
+    // Two pairs per thread only while it keeps 3 blocks per SM (W <= 4): at
+    // W = 5 (2 blocks) it measured 40% slower at e = 2, 150 bp.
+    if constexpr (VARIANT == 2 && W <= 4) {
+      if (a.m > 0) {
+        const uint64_t threads = (a.n_pairs + 1) / 2;
+        filter_pair2_kernel<W><<<(unsigned)((threads + kFilterThreads - 1) / kFilterThreads), kFilterThreads, 0,
+                                 stream>>>(a);
+        return cudaGetLastError();
+      }
+    }
     filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
     return cudaGetLastError();
   }

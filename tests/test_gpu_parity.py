@@ -102,6 +102,24 @@ def test_undefined_bases_both_layouts(m):
     assert_same(run.filter(), oracle_run(w), f"N m={m} per-pair e")
 
 
+@pytest.mark.parametrize("m", [17, 64, 100, 150, 250])
+def test_pairs_in_any_order(m):
+    """Pairs grouped by read (two neighbours share the read's shifted copies),
+    shuffled (each pair on its own) and half-shuffled, with an odd pair count
+    and invalid pairs among them."""
+    w = small_workload(m, 3001, seed=700 + m, cands=(1, 6))
+    rng = np.random.default_rng(m)
+    w.pair_read[rng.choice(w.n_pairs, 15, replace=False)] = w.n_reads + 1
+    half = np.arange(w.n_pairs)
+    half[: w.n_pairs // 2] = rng.permutation(w.n_pairs // 2)
+    for name, idx in (("grouped", np.arange(w.n_pairs)), ("shuffled", rng.permutation(w.n_pairs)),
+                      ("half", half)):
+        ws = w.subset(idx)
+        run = GpuRun(ws)
+        for e in (2, 3, 7, min(30, m - 1)):
+            assert_same(run.filter(e=e), oracle_run(ws, e), f"{name} m={m} e={e}")
+
+
 def test_invalid_pairs_and_error_counter():
     w = small_workload(100, 4000, seed=11, ref_len=50_000)
     L = w.ref.shape[0]
