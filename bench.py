@@ -401,7 +401,7 @@ def run_mine(args):
         "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, per_e_ms)},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
-                     "kernel": "filter_kernel<4, 1|2> (e 0-2 | 3-10)",
+                     "kernel": "filter_kernel<4, 1, 0> (e 0-1) | filter_pair2_kernel<4> (e 2-10)",
                      "peak_basis": f"{SM_COUNT} SMs x {ALU_LANES_PER_SM_CLK:.0f} int lanes/clk x {SM_MAX_MHZ:.0f} MHz",
                      "probe_measured_tops": {k: v / 1e12 for k, v in probe.items()},
                      "bytes_side": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
