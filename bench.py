@@ -21,6 +21,7 @@ the host cores instead, on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -659,6 +660,13 @@ def run_config5(args):
                      "mean_requests_per_round": float(np.mean(srv.coalesced)), "wall_s": wall,
                      "requests": len(reqs), "max_inflight_rounds": srv.max_inflight_seen})
         levels[str(load)] = summ
+    # the same 0.8 load with each round's inputs moved by one gk_gather kernel
+    cfg_g = dataclasses.replace(cfg, gather_inputs=True)
+    plan = serve.poisson_plan(args.requests, 0.8 * capacity / mean_size, 2103_14978 + 5 + 80)
+    reqs = [pool.request(q["id"], q["m"], q["e"], q["n_pairs"], q["start"], q["arrival"]) for q in plan]
+    srv = serve.Server(serve.GpuExecutor(gkref, cfg_g), cfg_g)
+    srv.run(reqs)
+    levels["0.8_gather_kernel"] = serve.latency_summary(reqs)
     line = {"metric": "serving: p50/p99 latency and pairs/s (config 5)", "unit": "Gpairs/s", "n_gpus": 1,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": "config 5: Poisson requests of 1k-1M pairs, m in {100,150,250}, "

@@ -219,6 +219,29 @@ int gk_copy_many(void *const *dst, const void *const *src, const uint64_t *bytes
                  uint32_t n, int kind, void *stream);
 
 /*
+ * gk_gather -- n copies done by one kernel instead of the copy engines, so
+ * that a coalesced launch moves many requests' small inputs without one
+ * copy-engine transfer per array (the continuous-batching analogue of the
+ * paper filling one batch from many reads, Sec. 3.5).  Two blocks per SM
+ * walk the entries; entry i copies bytes[i] bytes from src[i] to dst[i], with
+ * 16-byte accesses when both addresses have the same offset modulo 16, else
+ * 4-byte or 1-byte ones.
+ *   dst, src   n addresses the device can access: device memory, or
+ *              page-locked host memory (with unified addressing its host
+ *              pointer is valid on the device and the kernel reads it over
+ *              the host link)
+ *   bytes      n sizes, each at most GK_GATHER_MAX_BYTES (larger entries
+ *              are skipped: split them)
+ *   The three tables are read by the kernel, so they must be device memory
+ *   or page-locked host memory and stay unchanged until the kernel has run.
+ *   Overlapping source and destination ranges give undefined contents.
+ *   Asynchronous on `stream`.
+ */
+#define GK_GATHER_MAX_BYTES 65536u
+int gk_gather(const uint64_t *dst, const uint64_t *src, const uint64_t *bytes,
+              uint32_t n, void *stream);
+
+/*
  * gk_filter_batched_noalloc -- gk_filter_batched for callers that cannot
  * allocate device memory when they filter: for example a plugin inside a host
  * application whose device memory is all owned by the application's own

@@ -53,3 +53,80 @@ extern "C" int gk_copy_many(void *const *dst, const void *const *src, const uint
   }
   return GK_OK;
 }
+
+namespace {
+
+// Copies entry `at`: bytes[at] (<= GK_GATHER_MAX_BYTES) from src[at] to
+// dst[at] with 16-byte accesses when both addresses share their offset
+// modulo 16, else 4-byte accesses when they share it modulo 4, else bytes.
+__device__ __forceinline__ void gather_entry(const uint64_t *__restrict__ dst, const uint64_t *__restrict__ src,
+                                             const uint64_t *__restrict__ bytes, uint32_t at) {
+  const uint64_t n = bytes[at];
+  if (n == 0 || n > GK_GATHER_MAX_BYTES) return;
+  uint8_t *d = reinterpret_cast<uint8_t *>(dst[at]);
+  const uint8_t *s = reinterpret_cast<const uint8_t *>(src[at]);
+  const uint32_t t = threadIdx.x, nt = blockDim.x;
+  const uintptr_t rel = reinterpret_cast<uintptr_t>(s) ^ reinterpret_cast<uintptr_t>(d);
+  const uint32_t unit = (rel & 15) == 0 ? 16u : ((rel & 3) == 0 ? 4u : 1u);
+  // bytes before the first aligned unit, then whole units, then the tail
+  uint64_t head = (unit - (reinterpret_cast<uintptr_t>(s) & (unit - 1))) & (unit - 1);
+  if (head > n) head = n;
+  const uint64_t body = (n - head) / unit;
+  const uint64_t tail_at = head + body * unit;
+  for (uint64_t i = t; i < head; i += nt) d[i] = s[i];
+  if (unit == 16) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(s + head);
+    uint4 *d4 = reinterpret_cast<uint4 *>(d + head);
+    uint64_t i = t;
+    for (; i + 3 * nt < body; i += 4 * nt) {  // four loads in flight per thread
+      const uint4 a = s4[i], b = s4[i + nt], c = s4[i + 2 * nt], e = s4[i + 3 * nt];
+      d4[i] = a;
+      d4[i + nt] = b;
+      d4[i + 2 * nt] = c;
+      d4[i + 3 * nt] = e;
+    }
+    for (; i < body; i += nt) d4[i] = s4[i];
+  } else if (unit == 4) {
+    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(s + head);
+    uint32_t *d1 = reinterpret_cast<uint32_t *>(d + head);
+    uint64_t i = t;
+    for (; i + 3 * nt < body; i += 4 * nt) {
+      const uint32_t a = s1[i], b = s1[i + nt], c = s1[i + 2 * nt], e = s1[i + 3 * nt];
+      d1[i] = a;
+      d1[i + nt] = b;
+      d1[i + 2 * nt] = c;
+      d1[i + 3 * nt] = e;
+    }
+    for (; i < body; i += nt) d1[i] = s1[i];
+  } else {
+    for (uint64_t i = t; i < body; i += nt) d[head + i] = s[head + i];
+  }
+  for (uint64_t i = tail_at + t; i < n; i += nt) d[i] = s[i];
+}
+
+// A few blocks per SM walk the entries: enough loads in flight to fill the
+// host link without taking the SMs from a filter running on another stream.
+__global__ void __launch_bounds__(256) gather_kernel(const uint64_t *__restrict__ dst, const uint64_t *__restrict__ src,
+                                                     const uint64_t *__restrict__ bytes, uint32_t n) {
+  for (uint32_t at = blockIdx.x; at < n; at += gridDim.x) gather_entry(dst, src, bytes, at);
+}
+
+}  // namespace
+
+extern "C" int gk_gather(const uint64_t *dst, const uint64_t *src, const uint64_t *bytes, uint32_t n,
+                         void *stream) {
+  gk::clear_error();
+  if (n == 0) return GK_OK;
+  if (!dst || !src || !bytes) return gk::fail(GK_EINVAL, "gk_gather: null table");
+  if (n > 0x7fffffffu) return gk::fail(GK_ERANGE, "gk_gather: too many entries");
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+      sms = 132;
+  }
+  const uint32_t grid = n < 2u * (uint32_t)sms ? n : 2u * (uint32_t)sms;
+  gather_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(dst, src, bytes, n);
+  return gk::cuda_check(cudaGetLastError(), "gk_gather: launch");
+}

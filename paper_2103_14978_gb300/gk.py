@@ -60,6 +60,7 @@ _SIGS = {
     "gk_rebase_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                          _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_copy_many": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_int, _c.c_void_p], _c.c_int),
+    "gk_gather": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_pipe_create": ([_c.c_void_p, _c.POINTER(PipeDesc), _c.POINTER(_c.c_void_p)], _c.c_int),
     "gk_pipe_submit": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_uint64,
                         _c.c_void_p, _c.c_void_p, _c.POINTER(_c.c_uint64)], _c.c_int),
@@ -68,6 +69,7 @@ _SIGS = {
 }
 
 GK_NOALLOC_MAX_PAIRS = 1_000_000
+GK_GATHER_MAX_BYTES = 65536
 
 
 class Tiling(ctypes.Structure):
@@ -323,6 +325,34 @@ def gk_copy_many(dst: np.ndarray, src: np.ndarray, nbytes: np.ndarray, kind: int
     nbytes = np.ascontiguousarray(nbytes, np.uint64)
     _check(lib().gk_copy_many(dst.ctypes.data, src.ctypes.data, nbytes.ctypes.data, dst.shape[0], kind,
                               _stream(stream)))
+
+
+def gather_chunks(dst: np.ndarray, src: np.ndarray, nbytes: np.ndarray, chunk: int = GK_GATHER_MAX_BYTES):
+    """Split copies (uint64 address / size arrays) into gk_gather entries of
+    at most ``chunk`` bytes; returns the (dst, src, bytes) entry arrays."""
+    dst = np.asarray(dst, np.uint64)
+    src = np.asarray(src, np.uint64)
+    nb = np.asarray(nbytes, np.uint64)
+    keep = nb > 0
+    dst, src, nb = dst[keep], src[keep], nb[keep]
+    k = ((nb + np.uint64(chunk - 1)) // np.uint64(chunk)).astype(np.int64)
+    first = np.repeat(np.cumsum(k) - k, k)
+    which = np.repeat(np.arange(k.shape[0]), k)
+    off = (np.arange(int(k.sum()), dtype=np.int64) - first).astype(np.uint64) * np.uint64(chunk)
+    size = np.minimum(nb[which] - off, np.uint64(chunk))
+    return dst[which] + off, src[which] + off, size
+
+
+def gk_gather(dst: torch.Tensor, src: torch.Tensor, nbytes: torch.Tensor, n: int, stream=None):
+    """One kernel doing n copies (gk_gather).  The three tables are int64
+    tensors the device can read (CUDA, or pinned host), left unchanged until
+    the kernel has run; entries come from gather_chunks."""
+    for t, name in ((dst, "dst"), (src, "src"), (nbytes, "nbytes")):
+        if t.dtype != torch.int64 or not t.is_contiguous() or t.numel() < n:
+            raise ValueError(f"gk_gather: {name} must be a contiguous int64 tensor of >= n entries")
+        if not (t.is_cuda or t.is_pinned()):
+            raise ValueError(f"gk_gather: {name} must be device memory or pinned host memory")
+    _check(lib().gk_gather(dst.data_ptr(), src.data_ptr(), nbytes.data_ptr(), int(n), _stream(stream)))
 
 
 GK_PROBE_LOP3, GK_PROBE_SHF, GK_PROBE_MIX = 0, 1, 2

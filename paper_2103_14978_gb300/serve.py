@@ -162,6 +162,9 @@ class ServeConfig:
     tiling: tuple = (1, 256, 3, 8)
     round_timeout_s: float = 30.0     # host watchdog on a launched round
     copy_results: bool = True         # copy each request's results out of the result ring
+    gather_inputs: bool = False       # move a round's inputs with one gk_gather kernel instead of
+                                      # one copy-engine transfer per array and request
+    gather_entries: int = 1 << 17     # gather table capacity per stream (64 KiB entries)
 
 
 @dataclasses.dataclass
@@ -326,6 +329,9 @@ class GpuExecutor:
         self.h_sege = [torch.empty(max_req, dtype=torch.uint8, pin_memory=True) for _ in self.streams]
         self.d_seg = [e(2 * max_req, torch.int64) for _ in self.streams]
         self.d_sege = [e(max_req, torch.uint8) for _ in self.streams]
+        # per stream slot: gk_gather tables (dst | src | bytes), pinned so the kernel reads them directly
+        self.h_gather = [torch.empty(3 * config.gather_entries, dtype=torch.int64, pin_memory=True)
+                         for _ in self.streams]
         self.tiling = gk.Tiling(*config.tiling)
         self.ev0 = None
 
@@ -366,7 +372,7 @@ class GpuExecutor:
         dst += [dseg.data_ptr(), dseg.data_ptr() + 8 * M, dsege.data_ptr()]
         src += [self.h_seg[slot].data_ptr(), self.h_seg[slot].data_ptr() + 8 * M, self.h_sege[slot].data_ptr()]
         nb += [8 * n, 8 * n, n]
-        gk.gk_copy_many(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), gk.H2D, st)
+        self._copy_in(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), slot, st)
         for p0, np_, k0, ns in runs:
             gk.gk_rebase_pairs(self.pread[p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
                                pair_e=self.pe[p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
@@ -385,6 +391,28 @@ class GpuExecutor:
         ev_host = torch.cuda.Event(enable_timing=False)
         ev_host.record(st)
         return (ev_dev, ev_host)
+
+    def _copy_in(self, dst, src, nb, slot, st):
+        """Host-to-device copies of a round: by default one copy-engine
+        transfer per array and request; with `gather_inputs`, one gk_gather
+        kernel reading the pinned request buffers (208 GB/s on this pattern
+        against 135 GB/s for the copy engines on an idle GPU, but it needs
+        SMs: behind the other stream's persistent filter it waits, and the
+        server measured 4.06 against 4.52 Gpairs/s at 0.8 load)."""
+        gk = self.gk
+        if self.cfg.gather_inputs:
+            cd, cs, cn = gk.gather_chunks(dst, src, nb)
+            k = cd.shape[0]
+            cap = self.cfg.gather_entries
+            if k <= cap:
+                tab = self.h_gather[slot]
+                t = tab.numpy()
+                t[:k] = cd.view(np.int64)
+                t[cap:cap + k] = cs.view(np.int64)
+                t[2 * cap:2 * cap + k] = cn.view(np.int64)
+                gk.gk_gather(tab[:cap], tab[cap:2 * cap], tab[2 * cap:], k, st)
+                return
+        gk.gk_copy_many(dst, src, nb, gk.H2D, st)
 
     def done(self, handle) -> bool:
         return handle[1].query()

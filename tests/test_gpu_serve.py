@@ -70,3 +70,59 @@ def test_admission_under_a_small_memory_budget(setup):
     for r in served[::10]:
         a, e = oracle_of(ref, r)
         assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits), r.id
+
+
+def test_round_inputs_by_gather_kernel_or_copy_engines_agree(setup):
+    """The same requests served with their inputs moved by one gk_gather
+    kernel per round and by one copy-engine transfer per array give the same
+    results (tolerance 0)."""
+    ref, gkref, pool = setup
+    out = []
+    for gather in (True, False):
+        cfg = serve.ServeConfig(mem_cap_bytes=2 << 30, max_round_pairs=1_000_000, gather_inputs=gather)
+        reqs = requests(pool, 80, 40_000.0, 63)
+        serve.Server(serve.GpuExecutor(gkref, cfg), cfg).run(reqs)
+        assert all(r.status == "done" for r in reqs)
+        out.append(reqs)
+    for a, b in zip(*out):
+        assert np.array_equal(a.accept, b.accept) and np.array_equal(a.edits, b.edits), a.id
+
+
+def test_gather_kernel_copies_exactly():
+    """gk_gather through the C ABI: entries of 0..65536 bytes at every
+    relative alignment (16-, 4- and 1-byte paths), from pinned host memory
+    and from device memory, bytes outside the entries untouched, entries
+    above the maximum skipped."""
+    require_gpu()
+    rng = np.random.default_rng(8)
+    n_bytes = 8 << 20
+    host = torch.from_numpy(rng.integers(0, 256, n_bytes, dtype=np.uint8)).pin_memory()
+    dev_src = host.cuda()
+    for src_t in (host, dev_src):
+        dst = torch.full((n_bytes,), 0xAB, dtype=torch.uint8, device="cuda")
+        sizes = np.concatenate([[0, 1, 2, 3, 4, 15, 16, 17, 31, 33, 4095, 4096, 65535, 65536],
+                                rng.integers(0, 65537, 60)]).astype(np.int64)
+        want = np.full(n_bytes, 0xAB, np.uint8)
+        hs = host.numpy()
+        d_off, s_off, pos = [], [], 0
+        for k, z in enumerate(sizes):
+            so = int(rng.integers(0, n_bytes - 70_000))
+            do = pos + int(rng.integers(0, 32))  # destinations never overlap
+            pos = do + int(z) + 64
+            assert pos < n_bytes
+            d_off.append(do)
+            s_off.append(so)
+            want[do:do + z] = hs[so:so + z]
+        # one entry above the maximum: skipped
+        d_off.append(pos)
+        s_off.append(0)
+        sizes = np.append(sizes, 65537)
+        tab = torch.empty(3 * len(sizes), dtype=torch.int64, pin_memory=True)
+        t = tab.numpy()
+        n = len(sizes)
+        t[:n] = dst.data_ptr() + np.array(d_off, np.int64)
+        t[n:2 * n] = src_t.data_ptr() + np.array(s_off, np.int64)
+        t[2 * n:] = sizes
+        gk.gk_gather(tab[:n], tab[n:2 * n], tab[2 * n:], n)
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy(), want)

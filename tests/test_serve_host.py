@@ -155,3 +155,25 @@ def test_watchdog_stops_a_round_that_never_completes(pool):
     with pytest.raises(TimeoutError):
         serve_with(pool, reqs, never=True, round_timeout_s=0.05)
     assert any(r.status == "failed" for r in reqs)
+
+
+def test_gather_chunks_split_copies_into_bounded_entries():
+    from paper_2103_14978_gb300 import gk
+
+    rng = np.random.default_rng(5)
+    nb = np.concatenate([[0, 1, 65535, 65536, 65537, 3 * 65536], rng.integers(0, 400_000, 50)]).astype(np.uint64)
+    dst = (np.arange(nb.shape[0], dtype=np.uint64) << np.uint64(32)) + np.uint64(7)
+    src = (np.arange(nb.shape[0], dtype=np.uint64) << np.uint64(33)) + np.uint64(3)
+    cd, cs, cn = gk.gather_chunks(dst, src, nb)
+    assert (cn > 0).all() and (cn <= gk.GK_GATHER_MAX_BYTES).all()
+    assert int(cn.sum()) == int(nb.sum())
+    # entries tile every copy contiguously, in order
+    i = 0
+    for d, s, z in zip(dst, src, nb):
+        covered = 0
+        while covered < z:
+            assert cd[i] == d + np.uint64(covered) and cs[i] == s + np.uint64(covered)
+            covered += int(cn[i])
+            i += 1
+        assert covered == z
+    assert i == cd.shape[0]
