@@ -12,56 +12,81 @@ constexpr int kScatterChunk = 2048;  // pairs per scatter block
 
 constexpr int kClassifyChunk = 2048;  // pairs per classify block
 
-// kClassifyChunk pairs per block.  Invalid, undefined (N) and zero-length
-// pairs get their result here (Sec. 3.3 pass-through, the invalid sentinel)
-// and key kNoKey; the others get key (W, K) and are counted in the
-// block-local histogram.
+// kClassifyChunk pairs per block, kClassifyChunk / kPlanThreads per thread.
+// Invalid, undefined (N) and zero-length pairs get their result here (Sec.
+// 3.3 pass-through, the invalid sentinel) and key kNoKey; the others get key
+// (W, K) and are counted in the block-local histogram.  Each thread first
+// loads the ids of all its pairs, then every per-read and per-window word
+// they need (length, N flag, N index word; each only when its index is in
+// range), and only then decides: two rounds of independent loads instead of
+// a chain of dependent ones per pair.
 __global__ void __launch_bounds__(kPlanThreads) classify_kernel(const BatchArgs a) {
+  constexpr int R = kClassifyChunk / kPlanThreads;
   __shared__ uint32_t hist[kKeys];
   for (int i = threadIdx.x; i < kKeys; i += blockDim.x) hist[i] = 0;
   __syncthreads();
-  for (int it = 0; it < kClassifyChunk / kPlanThreads; ++it) {
-  const uint64_t p = (uint64_t)blockIdx.x * kClassifyChunk + (uint64_t)it * kPlanThreads + threadIdx.x;
-  const bool active = p < a.f.n_pairs;
-  int status = 0;  // 0 filter, 1 undefined, 2 invalid, 3 empty read
-  uint32_t key = kNoKey;
-  if (active) {
-    const uint32_t rid = a.f.pair_read[p];
-    const uint32_t off = a.f.pair_off[p];
-    const uint32_t e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : a.f.fixed_e;
-    uint32_t m = 0;
-    if ((uint64_t)rid >= a.f.n_reads) {
-      status = 2;
-    } else {
-      m = a.read_len[rid];
-      if (m > GK_MAX_LEN || m > 32u * a.f.stride_words || (uint64_t)off + m > a.f.ref_len) status = 2;
+  const uint64_t base = (uint64_t)blockIdx.x * kClassifyChunk + threadIdx.x;
+  uint32_t rid[R], off[R], e[R], m[R], nf[R];
+  uint2 ni[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint64_t p = base + (uint64_t)r * kPlanThreads;
+    rid[r] = 0xFFFFFFFFu;
+    off[r] = 0;
+    e[r] = a.f.fixed_e;
+    if (p < a.f.n_pairs) {
+      rid[r] = a.f.pair_read[p];
+      off[r] = a.f.pair_off[p];
+      if (a.f.pair_e) e[r] = a.f.pair_e[p];
     }
-    if (status == 0 && m == 0) status = 3;
-    if (status == 0) {
-      if (a.f.read_nflag && a.f.read_nflag[rid]) {
-        status = 1;
-      } else if (a.f.ref_nidx) {
-        const uint2 ni = a.f.ref_nidx[off >> 5];
-        const uint32_t q = ni.x >> (off & 31);
-        const uint64_t firstN = q ? (uint64_t)off + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
-        if (firstN < (uint64_t)off + m) status = 1;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    m[r] = 0;
+    nf[r] = 0;
+    ni[r] = make_uint2(0u, 0xFFFFFFFFu);
+    if ((uint64_t)rid[r] < a.f.n_reads) {
+      m[r] = a.read_len[rid[r]];
+      if (a.f.read_nflag) nf[r] = a.f.read_nflag[rid[r]];
+    }
+    if (a.f.ref_nidx && (uint64_t)off[r] < a.f.ref_len) ni[r] = a.f.ref_nidx[off[r] >> 5];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint64_t p = base + (uint64_t)r * kPlanThreads;
+    const bool active = p < a.f.n_pairs;
+    int status = 0;  // 0 filter, 1 undefined, 2 invalid, 3 empty read
+    uint32_t key = kNoKey;
+    if (active) {
+      const uint32_t mm = m[r];
+      if ((uint64_t)rid[r] >= a.f.n_reads || mm > GK_MAX_LEN || mm > 32u * a.f.stride_words ||
+          (uint64_t)off[r] + mm > a.f.ref_len)
+        status = 2;
+      if (status == 0 && mm == 0) status = 3;
+      if (status == 0) {
+        if (nf[r]) {
+          status = 1;
+        } else if (a.f.ref_nidx) {
+          const uint32_t q = ni[r].x >> (off[r] & 31);
+          const uint64_t firstN = q ? (uint64_t)off[r] + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni[r].y;
+          if (firstN < (uint64_t)off[r] + mm) status = 1;
+        }
       }
+      if (status == 0) {
+        const uint32_t W = (mm + 31) / 32;
+        const uint32_t K = min(e[r], 32u * W);
+        key = key_of(W, min(K, 255u));
+        atomicAdd(&hist[key], 1u);
+      } else {
+        a.f.accept[p] = status != 2;
+        a.f.edits[p] = status == 2 ? GK_EDITS_INVALID : (status == 1 ? GK_EDITS_UNDEFINED : 0);
+      }
+      a.s.km[p] = key | (mm << 16);
     }
-    if (status == 0) {
-      const uint32_t W = (m + 31) / 32;
-      const uint32_t K = min(e, 32u * W);
-      key = key_of(W, min(K, 255u));
-      atomicAdd(&hist[key], 1u);
-    } else {
-      a.f.accept[p] = status != 2;
-      a.f.edits[p] = status == 2 ? GK_EDITS_INVALID : (status == 1 ? GK_EDITS_UNDEFINED : 0);
+    if (a.f.err_count) {
+      const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
+      if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.f.err_count, (unsigned)__popc(bad));
     }
-    a.s.km[p] = key | (m << 16);
-  }
-  if (a.f.err_count) {
-    const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
-    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(a.f.err_count, (unsigned)__popc(bad));
-  }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kKeys; i += blockDim.x)
@@ -125,23 +150,37 @@ __global__ void __launch_bounds__(kPlanThreads) scatter_kernel(const BatchArgs a
   __shared__ uint32_t local[kKeys];
   for (int i = threadIdx.x; i < kKeys; i += blockDim.x) local[i] = 0;
   __syncthreads();
-  const uint64_t p0 = (uint64_t)blockIdx.x * kScatterChunk;
-  const uint64_t p1 = min_u64(p0 + kScatterChunk, a.f.n_pairs);
-  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const uint32_t k = a.s.km[p] & 0xFFFFu;
-    if (k != kNoKey) atomicAdd(&local[k], 1u);
+  constexpr int R = kScatterChunk / kPlanThreads;
+  const uint64_t p0 = (uint64_t)blockIdx.x * kScatterChunk + threadIdx.x;
+  uint32_t km[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint64_t p = p0 + (uint64_t)r * kPlanThreads;
+    km[r] = p < a.f.n_pairs ? a.s.km[p] : (uint32_t)kNoKey;
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if ((km[r] & 0xFFFFu) != kNoKey) atomicAdd(&local[km[r] & 0xFFFFu], 1u);
   __syncthreads();
   for (int i = threadIdx.x; i < kKeys; i += blockDim.x)
     if (local[i]) local[i] = atomicAdd(&a.s.cursor[i], local[i]);
   __syncthreads();
-  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const uint32_t km = a.s.km[p];
-    const uint32_t k = km & 0xFFFFu;
+  uint32_t rid[R], off[R], e[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint64_t p = p0 + (uint64_t)r * kPlanThreads;
+    if ((km[r] & 0xFFFFu) != kNoKey) {
+      rid[r] = a.f.pair_read[p];
+      off[r] = a.f.pair_off[p];
+      e[r] = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : min(a.f.fixed_e, 0xFFFFu);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t k = km[r] & 0xFFFFu;
     if (k != kNoKey) {
-      const uint32_t e = a.f.pair_e ? (uint32_t)a.f.pair_e[p] : min(a.f.fixed_e, 0xFFFFu);
-      a.s.rec[atomicAdd(&local[k], 1u)] =
-          make_uint4((uint32_t)p, a.f.pair_read[p], a.f.pair_off[p], e | (km & 0xFFFF0000u));
+      const uint64_t p = p0 + (uint64_t)r * kPlanThreads;
+      a.s.rec[atomicAdd(&local[k], 1u)] = make_uint4((uint32_t)p, rid[r], off[r], e[r] | (km[r] & 0xFFFF0000u));
     }
   }
 }
