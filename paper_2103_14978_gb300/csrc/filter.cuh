@@ -311,9 +311,16 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
 
   // ---- once per pair: end values of the AND, corrections, final erosion ----
   const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
-  const uint64_t RH = ((uint64_t)rh[W - 1] << 32) | (W >= 2 ? rh[W >= 2 ? W - 2 : 0] : 0u);
-  const uint64_t RL = ((uint64_t)rl[W - 1] << 32) | (W >= 2 ? rl[W >= 2 ? W - 2 : 0] : 0u);
-  const uint32_t tpos = tail + 32u;  // bit of position m in the 64-bit windows
+  const uint32_t r1k = rangeK & ~1u;       // bits 1..K
+  // The read's last 32 bases mirrored: bit j is position m-1-j (positions
+  // below 0 read as code 00).  The high end's terms are the low end's
+  // formulas on mirrored vectors, in 32-bit words.
+  const uint32_t xrh = __funnelshift_rc(W >= 2 ? rh[W >= 2 ? W - 2 : 0] : 0u, rh[W - 1], tail);
+  const uint32_t xrl = __funnelshift_rc(W >= 2 ? rl[W >= 2 ? W - 2 : 0] : 0u, rl[W - 1], tail);
+  const uint32_t b0h = 0u - (xrh >> 31), b0l = 0u - (xrl >> 31);                // R[m-1]
+  const uint32_t b1h = 0u - ((xrh >> 30) & 1u), b1l = 0u - ((xrl >> 30) & 1u);  // R[m-2]
+  const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);              // R[0]
+  const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);  // R[1]
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     // AND one base below position 0: every non-positive shift compares G[0]
@@ -321,17 +328,16 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     const uint32_t g0h = 0u - (gh[j][0] & 1u), g0l = 0u - (gl[j][0] & 1u);
     const uint32_t q0 = (rh[0] ^ g0h) | (rl[0] ^ g0l);
     const uint32_t vlo = ((~q0 & rangeK) == 0) ? 1u : 0u;
-    // Top two words as 64-bit windows; bit b is position 32(W-2) + b.
-    const uint64_t GH = ((uint64_t)gh[j][W - 1] << 32) | (W >= 2 ? gh[j][W >= 2 ? W - 2 : 0] : 0u);
-    const uint64_t GL = ((uint64_t)gl[j][W - 1] << 32) | (W >= 2 ? gl[j][W >= 2 ? W - 2 : 0] : 0u);
+    // The window's last 32 bases mirrored.
+    const uint32_t mgh = __brev(__funnelshift_rc(W >= 2 ? gh[j][W >= 2 ? W - 2 : 0] : 0u, gh[j][W - 1], tail));
+    const uint32_t mgl = __brev(__funnelshift_rc(W >= 2 ? gl[j][W >= 2 ? W - 2 : 0] : 0u, gl[j][W - 1], tail));
     // AND one base above position m-1, needed only when m fills the words:
     // every non-negative shift compares G[m-1] with R[m-1-i], i = 0..K.
     uint32_t vtop = 0u;
     if (tail == 32) {
-      const uint64_t gmh = 0ull - ((GH >> (tpos - 1)) & 1ull), gml = 0ull - ((GL >> (tpos - 1)) & 1ull);
-      const uint64_t qm = (RH ^ gmh) | (RL ^ gml);
-      const uint64_t rng = (((uint64_t)rangeK) << (tpos - 1 - K));
-      vtop = ((~qm & rng) == 0) ? 1u : 0u;
+      const uint32_t gmh = 0u - (mgh & 1u), gml = 0u - (mgl & 1u);
+      const uint32_t qm = (__brev(xrh) ^ gmh) | (__brev(xrl) ^ gml);
+      vtop = ((~qm & rangeK) == 0) ? 1u : 0u;
     }
     uint32_t f[W];
 #pragma unroll
@@ -342,30 +348,25 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     }
     // Low-end corrections (positions 1..K+1, word 0).
     {
-      const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);
-      const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);
       const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
       const uint32_t a0 = (gh[j][0] ^ r0h) | (gl[j][0] ^ r0l);
       const uint32_t a1 = ((gh[j][0] ^ r1h) | (gl[j][0] ^ r1l)) & v0;
       const uint32_t vac = gh[j][0] | gl[j][0];
       const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
       const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
-      const uint32_t r1k = rangeK & ~1u;
       f[0] &= ~((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));
     }
-    // High-end corrections (positions m-K-2..m-2, top two words).
+    // High-end corrections (positions m-K-2..m-2), computed mirrored and
+    // mapped back: mirrored bit j is position m-1-j.
     {
-      const uint64_t b0h = 0ull - ((RH >> (tpos - 1)) & 1ull), b0l = 0ull - ((RL >> (tpos - 1)) & 1ull);
-      const uint64_t b1h = 0ull - ((RH >> (tpos - 2)) & 1ull), b1l = 0ull - ((RL >> (tpos - 2)) & 1ull);
-      const uint64_t B0 = (GH ^ b0h) | (GL ^ b0l);
-      const uint64_t B1 = (GH ^ b1h) | (GL ^ b1l);
-      const uint64_t vac = GH | GL;
-      const uint64_t e1 = (B1 << 1) | B0 | (vac >> 1);
-      const uint64_t e2 = B0 | (vac >> 1) | (vac >> 2);
-      const uint64_t rh_range = ((1ull << (tpos - 1)) - 1ull) & ~((1ull << (tpos - K - 1)) - 1ull);
-      const uint64_t nc = (~(e1 & e2) & rh_range) | ((~e1 & rh_range) >> 1);
-      f[W - 1] &= ~(uint32_t)(nc >> 32);
-      if (W >= 2) f[W >= 2 ? W - 2 : 0] &= ~(uint32_t)nc;
+      const uint32_t a0 = (mgh ^ b0h) | (mgl ^ b0l);
+      const uint32_t a1 = (mgh ^ b1h) | (mgl ^ b1l);
+      const uint32_t vac = mgh | mgl;
+      const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
+      const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
+      const uint32_t nc = __brev((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));  // bit b: position m-32+b
+      f[W - 1] &= ~(nc >> (32u - tail));
+      if (W >= 2 && tail < 32) f[W >= 2 ? W - 2 : 0] &= ~(nc << tail);
     }
     f[W - 1] &= lastmask;
 
