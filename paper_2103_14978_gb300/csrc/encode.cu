@@ -13,7 +13,8 @@
 namespace gk {
 namespace {
 
-constexpr int kTileSeqs = 64;    // reads staged in shared memory per block
+constexpr int kMaxTileSeqs = 256;  // reads staged in shared memory per block, at most
+constexpr int kTileBytes = 32768;  // staged bytes per block aimed at (the tile shrinks for long rows)
 constexpr int kEncThreads = 256;
 constexpr int kTileSlack = 64;   // bytes past the tile an unaligned word gather may touch
 
@@ -54,22 +55,24 @@ __device__ __forceinline__ void encode32(const uint32_t (&wb)[8], uint32_t nvali
   }
 }
 
-// One block encodes kTileSeqs consecutive reads.  The tile's bytes are one
-// contiguous span of the input, staged into shared memory with 16-byte loads
-// where the span is aligned; each thread then builds whole words from shared
-// memory and the block ORs the undefined bits per read.
+// One block encodes tile_seqs (<= kMaxTileSeqs) consecutive reads.  The
+// tile's bytes are one contiguous span of the input, staged into shared
+// memory with 16-byte loads where the span is aligned (about 32 KiB per
+// block, so every thread has several loads in flight); each thread then
+// builds whole words from shared memory and the block ORs the undefined
+// bits per read.
 __global__ void __launch_bounds__(kEncThreads)
 encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const uint16_t *__restrict__ lens,
                     uint32_t fixed_len, uint64_t n_seq, uint32_t *__restrict__ packed,
-                    uint32_t stride_words, uint8_t *__restrict__ nflag) {
-  extern __shared__ __align__(16) uint8_t tile[];  // kTileSeqs * stride bytes
-  __shared__ uint32_t undef[kTileSeqs];
-  const uint64_t seq0 = (uint64_t)blockIdx.x * kTileSeqs;
-  const int nseq = (int)min_u64(kTileSeqs, n_seq - seq0);
+                    uint32_t stride_words, uint8_t *__restrict__ nflag, uint32_t tile_seqs) {
+  extern __shared__ __align__(16) uint8_t tile[];  // tile_seqs * stride bytes
+  __shared__ uint32_t undef[kMaxTileSeqs];
+  const uint64_t seq0 = (uint64_t)blockIdx.x * tile_seqs;
+  const int nseq = (int)min_u64(tile_seqs, n_seq - seq0);
   const uint8_t *src = ascii + seq0 * stride;
-  if (threadIdx.x < kTileSeqs) undef[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < nseq; i += blockDim.x) undef[i] = 0;
   // Bytes needed: up to the end of the last read's length (a length is never
-  // taken past the stride, so the tile holds at most kTileSeqs * stride).
+  // taken past the stride, so the tile holds at most tile_seqs * stride).
   const uint32_t last_len = lens ? lens[seq0 + nseq - 1] : fixed_len;
   const uint64_t need = (uint64_t)(nseq - 1) * stride + min_u64(last_len, stride);
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
@@ -106,7 +109,7 @@ encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const ui
     if (nb) atomicOr(&undef[s], 1u);
   }
   __syncthreads();
-  if (threadIdx.x < nseq) nflag[seq0 + threadIdx.x] = (uint8_t)(undef[threadIdx.x] != 0);
+  for (int i = threadIdx.x; i < nseq; i += blockDim.x) nflag[seq0 + i] = (uint8_t)(undef[i] != 0);
 }
 
 // One thread per 32-base word of a contiguous sequence (the reference): two
@@ -142,15 +145,19 @@ cudaError_t launch_encode_reads(const uint8_t *ascii, uint64_t ascii_stride, con
                                 uint16_t fixed_len, uint64_t n_seq, uint32_t *packed,
                                 uint32_t stride_words, uint8_t *nflag, cudaStream_t stream) {
   if (n_seq == 0) return cudaSuccess;
-  const uint64_t blocks = (n_seq + kTileSeqs - 1) / kTileSeqs;
-  const size_t smem = (size_t)kTileSeqs * ascii_stride + kTileSlack;
+  // about kTileBytes per block, 16..kMaxTileSeqs reads (ascii_stride <= 3072
+  // keeps the largest tile at 48 KiB)
+  uint64_t tile_seqs = kTileBytes / ascii_stride;
+  tile_seqs = tile_seqs < 16 ? 16 : (tile_seqs > kMaxTileSeqs ? kMaxTileSeqs : tile_seqs);
+  const uint64_t blocks = (n_seq + tile_seqs - 1) / tile_seqs;
+  const size_t smem = (size_t)tile_seqs * ascii_stride + kTileSlack;
   if (smem > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(encode_reads_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
   }
   encode_reads_kernel<<<(unsigned)blocks, kEncThreads, smem, stream>>>(
-      ascii, ascii_stride, lens, fixed_len, n_seq, packed, stride_words, nflag);
+      ascii, ascii_stride, lens, fixed_len, n_seq, packed, stride_words, nflag, (uint32_t)tile_seqs);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ namespace {
 
 constexpr uint64_t kMaxRefBases = (1ull << 32) - (1ull << 16);
 constexpr uint64_t kMaxPairs = (1ull << 31) * 128ull;  // grid x limit at 256 threads
-constexpr uint64_t kMaxDeviceAsciiStride = 3072;      // encoder tile: 64 reads in shared memory
+constexpr uint64_t kMaxDeviceAsciiStride = 3072;      // encoder tile: >= 16 rows in 48 KiB of shared memory
 
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
