@@ -55,6 +55,37 @@ __device__ __forceinline__ void encode32(const uint32_t (&wb)[8], uint32_t nvali
   }
 }
 
+// Fast form of encode32 for reads: the planes of the first `nvalid` bytes
+// of a word and whether any of them is not A/C/G/T (either case).  Per 4
+// bytes: bit 2 (high plane) and bit 1 XOR bit 2 (low plane) of each byte
+// are gathered into 4 consecutive bits by one multiply each; validity looks
+// up the letter the byte's bits 2 and 1 name ("A", "C", "T", "G" for 00, 01,
+// 10, 11) with two byte permutes and compares it with the case-folded byte.
+// When `bad` comes back non-zero the caller re-encodes the word with
+// encode32 (codes 00 for the undefined bytes).
+__device__ __forceinline__ void encode32_fast(const uint32_t (&wb)[8], uint32_t nvalid, uint32_t &hi,
+                                              uint32_t &lo, uint32_t &bad) {
+  hi = lo = bad = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t c = wb[j];
+    const uint32_t h = c & 0x04040404u;
+    const uint32_t l = (c ^ (c << 1)) & 0x04040404u;
+    // bits 2, 10, 18, 26 -> bits 24..27
+    hi |= ((h * 0x00408102u) >> 24) << (4 * j);
+    lo |= ((l * 0x00408102u) >> 24) << (4 * j);
+    const uint32_t idx = (c >> 1) & 0x03030303u;
+    const uint32_t sel = __byte_perm(idx | (idx >> 4), 0u, 0x4420u);
+    const uint32_t expect = __byte_perm(0x47544341u, 0u, sel);  // 'A' 'C' 'T' 'G'
+    const int rem = (int)nvalid - 4 * j;
+    const uint32_t keep = rem >= 4 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << (8 * rem)) - 1u));
+    bad |= ((c & 0xDFDFDFDFu) ^ expect) & keep;
+  }
+  const uint32_t m = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
+  hi &= m;
+  lo &= m;
+}
+
 // One block encodes tile_seqs (<= kMaxTileSeqs) consecutive reads.  The
 // tile's bytes are one contiguous span of the input, staged into shared
 // memory with 16-byte loads where the span is aligned (about 32 KiB per
@@ -102,7 +133,9 @@ encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const ui
       uint32_t wb[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) wb[j] = __funnelshift_r(src[j], src[j + 1], sh);
-      encode32(wb, rem >= 32 ? 32u : (uint32_t)rem, hi, lo, nb);
+      const uint32_t nv = rem >= 32 ? 32u : (uint32_t)rem;
+      encode32_fast(wb, nv, hi, lo, nb);
+      if (nb) encode32(wb, nv, hi, lo, nb);  // a non-ACGT byte: exact per-base path
     }
     uint32_t *out = packed + ((seq0 + s) * (uint64_t)stride_words + w) * 2;
     *reinterpret_cast<uint2 *>(out) = make_uint2(hi, lo);

@@ -195,6 +195,39 @@ def test_device_encoder_matches_host_encoder():
         assert torch.equal(hp2, fp.cpu()) and torch.equal(hn2, fn.cpu())
 
 
+def test_device_encoder_every_byte_value_and_rare_undefined_bases():
+    """Device encoder against the host encoder where most 32-base words are
+    all A/C/G/T in either case (its fast path) and a few hold one other byte;
+    and every byte value 0..255 at several positions of a read."""
+    rng = np.random.default_rng(9)
+    valid = np.frombuffer(b"ACGTacgt", np.uint8)
+    others = np.setdiff1d(np.arange(256, dtype=np.uint8), valid)
+    for stride, maxlen in ((100, 100), (97, 97), (150, 150), (256, 250), (333, 320)):
+        n = 3000
+        lens = rng.integers(0, maxlen + 1, n).astype(np.uint16)
+        asc = rng.choice(valid, n * stride)
+        hit = rng.random(n * stride) < 0.002
+        asc[hit] = rng.choice(others, int(hit.sum()))
+        sw = gk.words_for(maxlen)
+        hp, hn = gk.gk_encode(torch.from_numpy(asc), n, stride, lens=dd.as_i16(lens), stride_words=sw)
+        dp, dn = gk.gk_encode(torch.from_numpy(asc).cuda(), n, stride, lens=dd.as_i16(lens).cuda(),
+                              stride_words=sw)
+        torch.cuda.synchronize()
+        assert torch.equal(hp, dp.cpu()) and torch.equal(hn, dn.cpu()), stride
+        assert 0 < int(hn.sum()) < n
+    # every byte value at positions 0, 13, 31, 32, 63 and 99 of a 100-base read
+    pos = (0, 13, 31, 32, 63, 99)
+    n = 256 * len(pos)
+    asc = rng.choice(valid, n * 100)
+    for i, (b, k) in enumerate((b, k) for b in range(256) for k in pos):
+        asc[i * 100 + k] = b
+    hp, hn = gk.gk_encode(torch.from_numpy(asc), n, 100, fixed_len=100, stride_words=4)
+    dp, dn = gk.gk_encode(torch.from_numpy(asc).cuda(), n, 100, fixed_len=100, stride_words=4)
+    torch.cuda.synchronize()
+    assert torch.equal(hp, dp.cpu()) and torch.equal(hn, dn.cpu())
+    assert int(hn.sum()) == len(others) * len(pos)
+
+
 def test_config2_structure_scaled():
     """Config 2's structure (duplicated genome regions, 4 candidates per read,
     1 true origin) at 1/500 of its size, over the whole e sweep 0..10."""
