@@ -380,6 +380,8 @@ def run_mine(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world)
+        split = run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=False)
+        e2e["split_results"] = {k: split[k] for k in ("value", "d2h_bytes_per_step", "ms_per_step", "results")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,13 +419,15 @@ def run_mine(args):
         dist.destroy_process_group()
 
 
-def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
+def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True):
     """Same metric through the streamed pipeline of the public API (gk_pipe_*)
     from pinned host buffers: every step copies the ASCII reads and the pairs
     in, encodes them on the device, filters at e = 0..10 and copies every
-    result out.  Three steps are in flight, so one step's copies overlap
-    another's filtering; the timed region runs from the first submit to the
-    last step's results in host memory (wall clock, slowest rank)."""
+    result out (one result byte per pair and threshold with
+    GK_FLAG_RESULT_BYTE, else accept bytes and 16-bit counts).  Three steps
+    are in flight, so one step's copies overlap another's filtering; the
+    timed region runs from the first submit to the last step's results in
+    host memory (wall clock, slowest rank)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     h_asc = torch.from_numpy(w.reads).pin_memory()
     h_pr = dd.as_i32(w.pair_read).pin_memory()
@@ -431,8 +435,10 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
     n = w.n_pairs
     slots = 3
     outs = [(torch.empty(len(E_SWEEP) * n, dtype=torch.uint8).pin_memory(),
-             torch.empty(len(E_SWEEP) * n, dtype=torch.int16).pin_memory()) for _ in range(slots)]
-    pipe = gk.Pipe(ref, w.n_reads, w.stride, m, n, E_SWEEP, n_slots=slots)
+             None if result_byte else torch.empty(len(E_SWEEP) * n, dtype=torch.int16).pin_memory())
+            for _ in range(slots)]
+    pipe = gk.Pipe(ref, w.n_reads, w.stride, m, n, E_SWEEP, n_slots=slots,
+                   flags=gk.GK_FLAG_RESULT_BYTE if result_byte else 0)
 
     def run(k_steps):
         tickets = []
@@ -455,11 +461,14 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world):
     ms = reduce_max(wall_ms, world, dev)
     pipe.close()
     h2d = h_asc.numel() + 4 * n * 2
-    d2h = len(E_SWEEP) * n * 3
+    d2h = len(E_SWEEP) * n * (1 if result_byte else 3)
+    fmt = ("one result byte per pair and threshold (count capped at 253 or a sentinel; accept = byte <= e "
+           "or undefined)" if result_byte else "accept byte + 16-bit count per pair and threshold")
     return {"value": whole_job_rate(n * len(E_SWEEP), world, steps, ms), "unit": "Gpairs/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": ms / steps,
             "path": "pinned host ASCII reads + pairs -> gk_pipe (copy-in, device encode, 11 x gk_filter, "
-                    "copy-out on three streams, 3 steps in flight) -> results in pinned host memory"}
+                    "copy-out on three streams, 3 steps in flight) -> results in pinned host memory",
+            "results": fmt}
 
 
 def parse_es(spec: str):

@@ -51,6 +51,15 @@ extern "C" {
 
 #define GK_FLAG_NO_EDGE_FIX 1u /* skip the Sec. 3.4 improvement (the original
                                   GateKeeper), for accuracy comparisons */
+#define GK_FLAG_RESULT_BYTE 2u /* one result byte per pair in accept_out (no
+                                  edits_out): see gk_filter */
+
+/* Result bytes of GK_FLAG_RESULT_BYTE: a filtered pair's count capped at
+ * GK_RESULT_MAX_COUNT, or one of the two sentinels.  With a threshold
+ * e <= 252 the pair is accepted iff byte <= e or byte == GK_RESULT_UNDEFINED. */
+#define GK_RESULT_MAX_COUNT 253u
+#define GK_RESULT_UNDEFINED 254u /* non-ACGT base in the read or window: accepted */
+#define GK_RESULT_INVALID 255u   /* read id or window out of range: rejected */
 
 #define GK_EDITS_UNDEFINED 0xFFFFu /* pair holds a non-ACGT base: accept = 1 */
 #define GK_EDITS_INVALID 0xFFFEu   /* read id or window out of range: accept = 0 */
@@ -129,10 +138,15 @@ int gk_reference_info(gk_ref_t ref, uint64_t *n_bases, uint64_t *n_undefined);
  *   pair_e       device, n_pairs uint8 thresholds, or NULL to use fixed_e
  *   fixed_e      threshold for every pair when pair_e is NULL (0..255)
  *   count_mode   GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT
- *   flags        0 or GK_FLAG_NO_EDGE_FIX
- *   accept_out   device, n_pairs uint8: 1 accept, 0 reject
+ *   flags        0, GK_FLAG_NO_EDGE_FIX and/or GK_FLAG_RESULT_BYTE
+ *   accept_out   device, n_pairs uint8: 1 accept, 0 reject; with
+ *                GK_FLAG_RESULT_BYTE instead the pair's result byte: its
+ *                count capped at GK_RESULT_MAX_COUNT, GK_RESULT_UNDEFINED or
+ *                GK_RESULT_INVALID (a third of the bytes to move; it needs
+ *                pair_e NULL and fixed_e <= 252, else GK_EINVAL / GK_ERANGE)
  *   edits_out    device, n_pairs uint16: the error count (not clamped at e),
- *                GK_EDITS_UNDEFINED or GK_EDITS_INVALID
+ *                GK_EDITS_UNDEFINED or GK_EDITS_INVALID; unused (may be NULL)
+ *                with GK_FLAG_RESULT_BYTE
  *   err_count    device uint32 or NULL: incremented once per invalid pair
  *                (read id >= n_reads or off + m > reference length)
  * Asynchronous on `stream`; n_pairs == 0 enqueues nothing.  Host-side
@@ -303,7 +317,8 @@ typedef struct {
   uint32_t n_thresholds;       /* filter passes per batch, 1..64 */
   const uint8_t *thresholds;   /* host, n_thresholds values of e (copied at creation) */
   int count_mode;              /* GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT */
-  uint32_t flags;              /* 0 or GK_FLAG_NO_EDGE_FIX */
+  uint32_t flags;              /* 0, GK_FLAG_NO_EDGE_FIX, GK_FLAG_RESULT_BYTE
+                                  (then every threshold <= 252) */
   uint32_t n_slots;            /* batches in flight, 2..4 */
 } gk_pipe_desc_t;
 
@@ -317,8 +332,10 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *desc, gk_pipe_t *out);
  *   ascii       host, n_reads * ascii_stride bytes (read i at i*ascii_stride)
  *   pair_read   host, n_pairs uint32 read ids (within this batch)
  *   pair_off    host, n_pairs uint32 reference offsets
- *   accept_out  host, n_thresholds * n_pairs uint8, threshold-major
- *   edits_out   host, n_thresholds * n_pairs uint16, threshold-major
+ *   accept_out  host, n_thresholds * n_pairs uint8, threshold-major (the
+ *               result bytes with GK_FLAG_RESULT_BYTE)
+ *   edits_out   host, n_thresholds * n_pairs uint16, threshold-major; unused
+ *               (may be NULL) with GK_FLAG_RESULT_BYTE
  *   ticket      receives the batch's number (0, 1, 2, ... per pipe)
  * Results are in accept_out / edits_out once gk_pipe_wait(ticket) returns;
  * all five host buffers must stay valid and unchanged until then.  Copies

@@ -441,15 +441,28 @@ __device__ __forceinline__ int pair_status(const FilterArgs &a, const PairData<W
 }
 
 __device__ __forceinline__ void write_trivial(const FilterArgs &a, uint64_t p, int status) {
+  if (a.result_byte) {
+    a.accept[p] = status == 0 ? 0 : (status == 1 ? GK_RESULT_UNDEFINED : GK_RESULT_INVALID);
+    return;
+  }
   a.accept[p] = status != 2;
   a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+}
+
+// The result of a filtered pair: accept bit and count, or the result byte.
+__device__ __forceinline__ void write_count(const FilterArgs &a, uint64_t p, uint32_t count, uint32_t e) {
+  if (a.result_byte) {
+    a.accept[p] = (uint8_t)min(count, GK_RESULT_MAX_COUNT);
+    return;
+  }
+  a.accept[p] = count <= e;
+  a.edits[p] = (uint16_t)count;
 }
 
 template <int W, int VARIANT>
 __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p, const PairData<W> &x) {
   const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, x) : filter_loaded<W, VARIANT == 1>(a, x);
-  a.accept[p] = count <= x.e;
-  a.edits[p] = (uint16_t)count;
+  write_count(a, p, count, x.e);
 }
 
 // The classify phase of the compacting loop, in two steps so that the loads
@@ -717,10 +730,8 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
       gl[1][W - 1] &= lastmask;
     }
     deferred_counts<W, 2>(a, a.m, min(a.fixed_e, a.m - 1), rh, rl, gh, gl, count);
-    a.accept[p0] = count[0] <= a.fixed_e;
-    a.edits[p0] = (uint16_t)count[0];
-    a.accept[p1] = count[1] <= a.fixed_e;
-    a.edits[p1] = (uint16_t)count[1];
+    write_count(a, p0, count[0], a.fixed_e);
+    write_count(a, p1, count[1], a.fixed_e);
   } else {
     if (s0 == 0) filter_and_write<W, 2>(a, p0, x0);
     if (s1 == 0) filter_and_write<W, 2>(a, p1, x1);

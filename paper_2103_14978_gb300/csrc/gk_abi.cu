@@ -214,15 +214,20 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   if (m > GK_MAX_LEN) return fail(GK_ERANGE, "gk_filter: m above GK_MAX_LEN");
   if (n_pairs == 0) return GK_OK;
   if (n_pairs > kMaxPairs) return fail(GK_ERANGE, "gk_filter: too many pairs for one launch");
-  if (!pair_read || !pair_off || !accept_out || !edits_out)
+  const bool result_byte = (flags & GK_FLAG_RESULT_BYTE) != 0;
+  if (!pair_read || !pair_off || !accept_out || (!edits_out && !result_byte))
     return fail(GK_EINVAL, "gk_filter: null pair or output buffer");
+  if (result_byte && pair_e)
+    return fail(GK_EINVAL, "gk_filter: GK_FLAG_RESULT_BYTE needs one threshold (pair_e NULL)");
+  if (result_byte && fixed_e > 252)
+    return fail(GK_ERANGE, "gk_filter: GK_FLAG_RESULT_BYTE needs fixed_e <= 252");
   const uint32_t W = m == 0 ? 1 : (m + 31) / 32;
   if (m > 0 && (!reads || stride_words < W))
     return fail(GK_EINVAL, "gk_filter: reads missing or stride_words < ceil(m/32)");
   if (!pair_e && fixed_e > 255) return fail(GK_ERANGE, "gk_filter: fixed_e above 255");
   if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
     return fail(GK_EINVAL, "gk_filter: unknown count_mode");
-  if (flags & ~GK_FLAG_NO_EDGE_FIX) return fail(GK_EINVAL, "gk_filter: unknown flags");
+  if (flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE)) return fail(GK_EINVAL, "gk_filter: unknown flags");
   if (reads && !aligned(reads, 8)) return fail(GK_EINVAL, "gk_filter: reads must be 8-byte aligned");
   gk::FilterArgs a{};
   a.ref_hl = ref->hl;
@@ -240,6 +245,7 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.n_pairs = n_pairs;
   a.count_mode = count_mode;
   a.edge_on = (flags & GK_FLAG_NO_EDGE_FIX) ? 0 : 1;
+  a.result_byte = result_byte ? 1 : 0;
   a.accept = accept_out;
   a.edits = edits_out;
   a.err_count = err_count;

@@ -60,6 +60,7 @@ struct FilterArgs {
   uint16_t *edits;
   uint32_t *err_count;  // nullable
   int compact;          // plain filter: persistent warps that filter only defined pairs
+  int result_byte;      // accept receives one result byte per pair (GK_FLAG_RESULT_BYTE)
 };
 
 // Launches the plain filter for words-per-read W = ceil(m/32) (1..16).

@@ -111,7 +111,11 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
     return gk::fail(GK_EINVAL, "gk_pipe_create: n_thresholds must be 1..64 with a threshold array");
   if (d->count_mode != GK_COUNT_RUNS4 && d->count_mode != GK_COUNT_POPCOUNT)
     return gk::fail(GK_EINVAL, "gk_pipe_create: unknown count_mode");
-  if (d->flags & ~GK_FLAG_NO_EDGE_FIX) return gk::fail(GK_EINVAL, "gk_pipe_create: unknown flags");
+  if (d->flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE))
+    return gk::fail(GK_EINVAL, "gk_pipe_create: unknown flags");
+  if (d->flags & GK_FLAG_RESULT_BYTE)
+    for (uint32_t i = 0; i < d->n_thresholds; ++i)
+      if (d->thresholds[i] > 252) return gk::fail(GK_ERANGE, "gk_pipe_create: GK_FLAG_RESULT_BYTE needs e <= 252");
   if (d->n_slots < 2 || d->n_slots > kMaxSlots) return gk::fail(GK_EINVAL, "gk_pipe_create: n_slots must be 2..4");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return gk::fail(GK_ECUDA, "gk_pipe_create: cudaGetDevice failed");
@@ -139,7 +143,7 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
     ok = alloc(&s.ascii, p->max_reads * p->ascii_stride) && alloc(&s.pair_read, 4 * p->max_pairs) &&
          alloc(&s.pair_off, 4 * p->max_pairs) && alloc(&s.packed, 8ull * p->stride_words * p->max_reads) &&
          alloc(&s.nflag, p->max_reads) && alloc(&s.accept, n_th * p->max_pairs) &&
-         alloc(&s.edits, 2 * n_th * p->max_pairs) &&
+         ((p->flags & GK_FLAG_RESULT_BYTE) || alloc(&s.edits, 2 * n_th * p->max_pairs)) &&
          cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&s.run_done, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&s.out_done, cudaEventDisableTiming) == cudaSuccess;
@@ -161,7 +165,8 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
   if (p->sticky != GK_OK) return gk::fail(p->sticky, "gk_pipe_submit: the pipe failed earlier");
   if (n_reads > p->max_reads || n_pairs > p->max_pairs)
     return gk::fail(GK_ERANGE, "gk_pipe_submit: batch larger than the pipe's max_reads / max_pairs");
-  if ((n_reads && !ascii) || (n_pairs && (!pair_read || !pair_off || !accept_out || !edits_out)))
+  const bool result_byte = (p->flags & GK_FLAG_RESULT_BYTE) != 0;
+  if ((n_reads && !ascii) || (n_pairs && (!pair_read || !pair_off || !accept_out || (!edits_out && !result_byte))))
     return gk::fail(GK_EINVAL, "gk_pipe_submit: null host buffer");
   DeviceGuard guard(p->device);
   if (guard.err != cudaSuccess) return broken(p, GK_ECUDA, "gk_pipe_submit: cannot make the pipe's device current");
@@ -196,7 +201,8 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
   for (uint64_t i = 0; i < n_th && n_pairs; ++i) {
     const int rc = gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read,
                              s.pair_off, nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags,
-                             s.accept + i * n_pairs, s.edits + i * n_pairs, nullptr, p->s_run);
+                             s.accept + i * n_pairs, result_byte ? nullptr : s.edits + i * n_pairs, nullptr,
+                             p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
   if (!cuda(cudaEventRecord(s.run_done, p->s_run), "event")) return p->sticky;
@@ -204,8 +210,9 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
   if (!cuda(cudaStreamWaitEvent(p->s_out, s.run_done, 0), "wait for the run")) return p->sticky;
   if (n_pairs && !(cuda(cudaMemcpyAsync(accept_out, s.accept, n_th * n_pairs, cudaMemcpyDeviceToHost, p->s_out),
                         "copy of the accept bits") &&
-                   cuda(cudaMemcpyAsync(edits_out, s.edits, 2 * n_th * n_pairs, cudaMemcpyDeviceToHost, p->s_out),
-                        "copy of the edit counts")))
+                   (result_byte ||
+                    cuda(cudaMemcpyAsync(edits_out, s.edits, 2 * n_th * n_pairs, cudaMemcpyDeviceToHost, p->s_out),
+                         "copy of the edit counts"))))
     return p->sticky;
   if (!cuda(cudaEventRecord(s.out_done, p->s_out), "event")) return p->sticky;
   s.used = true;

@@ -18,6 +18,8 @@ GK_MAX_LEN = 512
 GK_OK, GK_EINVAL, GK_ERANGE, GK_ENOMEM, GK_ECUDA = 0, -1, -2, -3, -4
 GK_COUNT_RUNS4, GK_COUNT_POPCOUNT = 0, 1
 GK_FLAG_NO_EDGE_FIX = 1
+GK_FLAG_RESULT_BYTE = 2
+GK_RESULT_MAX_COUNT, GK_RESULT_UNDEFINED, GK_RESULT_INVALID = 253, 254, 255
 GK_EDITS_UNDEFINED, GK_EDITS_INVALID = 0xFFFF, 0xFFFE
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgk.so")
@@ -223,12 +225,13 @@ def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: i
     """Filter pairs of read length m (gk_filter).  ``e`` is an int or a CUDA
     uint8 tensor (one threshold per pair).  ``pair_read``/``pair_off`` are
     int32 CUDA tensors read as uint32.  Returns (accept uint8, edits int16 read
-    as uint16)."""
+    as uint16); with GK_FLAG_RESULT_BYTE, (result bytes uint8, None)."""
     n = pair_read.numel()
     dev = pair_read.device
+    result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
     if accept is None:
         accept = torch.empty(n, dtype=torch.uint8, device=dev)
-    if edits is None:
+    if edits is None and not result_byte:
         edits = torch.empty(n, dtype=torch.int16, device=dev)
     if m > 0 and reads.numel() < n_reads * stride_words * 2:
         raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
@@ -243,9 +246,14 @@ def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: i
         _dptr(read_nflag, torch.uint8, "read_nflag", n_reads), m,
         _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n),
         pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
-        _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1),
-        _stream(stream)))
-    return accept, edits
+        None if result_byte else _dptr(edits, torch.int16, "edits", n),
+        _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    return accept, (None if result_byte else edits)
+
+
+def accept_of_result_bytes(res: torch.Tensor, e: int) -> torch.Tensor:
+    """Accept bits of GK_FLAG_RESULT_BYTE results at threshold e (<= 252)."""
+    return ((res <= e) | (res == GK_RESULT_UNDEFINED)).to(torch.uint8)
 
 
 def gk_filter_batched_workspace(n_pairs: int) -> int:
@@ -400,6 +408,7 @@ class Pipe:
         self.ref = ref
         self.ascii_stride = ascii_stride
         self.n_thresholds = int(th.size)
+        self.result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
         self._held = {}
 
     def submit(self, ascii, n_reads: int, pair_read, pair_off, accept_out, edits_out) -> int:
@@ -408,6 +417,7 @@ class Pipe:
         args = (_hptr(ascii, (torch.uint8,), "ascii", n_reads * self.ascii_stride), n_reads,
                 _hptr(pair_read, i32, "pair_read", n_pairs), _hptr(pair_off, i32, "pair_off", n_pairs), n_pairs,
                 _hptr(accept_out, (torch.uint8,), "accept_out", self.n_thresholds * n_pairs),
+                None if self.result_byte else
                 _hptr(edits_out, (torch.int16,), "edits_out", self.n_thresholds * n_pairs))
         t = ctypes.c_uint64()
         _check(lib().gk_pipe_submit(self.handle, *args, ctypes.byref(t)))

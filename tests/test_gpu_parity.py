@@ -120,6 +120,39 @@ def test_pairs_in_any_order(m):
             assert_same(run.filter(e=e), oracle_run(ws, e), f"{name} m={m} e={e}")
 
 
+@pytest.mark.parametrize("m", [31, 100, 150, 250])
+def test_result_byte_format(m):
+    """GK_FLAG_RESULT_BYTE: each pair's byte is its count capped at 253, 254
+    for undefined and 255 for invalid pairs, on both layouts (genome with N),
+    against the split results and the oracle; the flag's argument rules."""
+    w = small_workload(m, 5000, seed=1100 + m, n_frac=0.001, read_n_frac=0.001, cands=(1, 8))
+    w.pair_read[:25] = w.n_reads + 2
+    run = GpuRun(w)
+    r = run.reads
+    for e in (0, 1, 2, 5, 9, min(252, m - 1), 252):
+        a, d = run.filter(e=e)
+        res, none = gk.gk_filter(run.ref, r.packed, r.stride_words, r.n_reads, r.nflag, m,
+                                 run.pairs.pair_read, run.pairs.pair_off, e, flags=gk.GK_FLAG_RESULT_BYTE)
+        torch.cuda.synchronize()
+        assert none is None
+        d64 = d.astype(np.int64)
+        want = np.minimum(d64, 253)
+        want[d64 == O.UNDEFINED] = 254
+        want[d64 == O.INVALID] = 255
+        assert np.array_equal(res.cpu().numpy(), want.astype(np.uint8)), f"m={m} e={e}"
+        assert np.array_equal(gk.accept_of_result_bytes(res, e).cpu().numpy(), a)
+        assert_same((a, d), oracle_run(w, e), f"m={m} e={e}")
+    with pytest.raises(gk.GKError) as exc:
+        gk.gk_filter(run.ref, r.packed, r.stride_words, r.n_reads, r.nflag, m, run.pairs.pair_read,
+                     run.pairs.pair_off, 253, flags=gk.GK_FLAG_RESULT_BYTE)
+    assert exc.value.code == gk.GK_ERANGE
+    pe = torch.full((w.n_pairs,), 3, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gk.GKError) as exc:
+        gk.gk_filter(run.ref, r.packed, r.stride_words, r.n_reads, r.nflag, m, run.pairs.pair_read,
+                     run.pairs.pair_off, pe, flags=gk.GK_FLAG_RESULT_BYTE)
+    assert exc.value.code == gk.GK_EINVAL
+
+
 def test_invalid_pairs_and_error_counter():
     w = small_workload(100, 4000, seed=11, ref_len=50_000)
     L = w.ref.shape[0]

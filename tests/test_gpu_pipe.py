@@ -88,3 +88,41 @@ def test_pipe_reuses_slots_many_times_and_rejects_oversize():
         pipe.wait(10_000)
     pipe.close()
     ref.close()
+
+
+def _result_bytes_of(acc, ed):
+    """Expected GK_FLAG_RESULT_BYTE bytes from the split results."""
+    ed = ed.astype(np.int64)
+    out = np.minimum(ed, gk.GK_RESULT_MAX_COUNT)
+    out[ed == gk.GK_EDITS_UNDEFINED] = gk.GK_RESULT_UNDEFINED
+    out[ed == gk.GK_EDITS_INVALID] = gk.GK_RESULT_INVALID
+    return out.astype(np.uint8)
+
+
+def test_pipe_result_bytes_equal_the_oracle():
+    """GK_FLAG_RESULT_BYTE through the pipe: one byte per pair and threshold,
+    no edit counts moved; each byte is the oracle's count (capped at 253) or
+    a sentinel, and decides accept exactly."""
+    require_gpu()
+    w = synth.config2(scale=0.001, ref_bases=2_000_000)
+    ref = gk.gk_load_reference(w.ref)
+    bs = batches_of(w, [0, 1500, 3100, w.n_reads])
+    max_reads = max(b[1] for b in bs)
+    max_pairs = max(b[2].size for b in bs)
+    want = {e: oracle_run(w, e) for e in THRESHOLDS}
+    with gk.Pipe(ref, max_reads, w.stride, 100, max_pairs, THRESHOLDS, flags=gk.GK_FLAG_RESULT_BYTE) as pipe:
+        jobs = []
+        for asc, nr, pr, po, idx in bs:
+            res = torch.empty(len(THRESHOLDS) * pr.size, dtype=torch.uint8).pin_memory()
+            jobs.append((pipe.submit(pinned(asc), nr, pinned(pr), pinned(po), res, None), res, idx))
+        pipe.wait(jobs[-1][0])
+        for t, res, idx in jobs:
+            r = res.numpy().reshape(len(THRESHOLDS), idx.size)
+            for i, e in enumerate(THRESHOLDS):
+                wa, we = want[e][0][idx], want[e][1][idx]
+                assert np.array_equal(r[i], _result_bytes_of(wa, we)), f"batch {t} e={e}"
+                acc = gk.accept_of_result_bytes(torch.from_numpy(r[i]), e).numpy()
+                assert np.array_equal(acc, wa), f"batch {t} e={e}"
+    with pytest.raises(gk.GKError):
+        gk.Pipe(ref, 10, w.stride, 100, 10, (3, 253), flags=gk.GK_FLAG_RESULT_BYTE)
+    ref.close()
