@@ -377,6 +377,27 @@ def run_mine(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     probe = probe_alu(torch, gk, stream, args.probe_all)
 
+    # the paper's device-encoded mode at one threshold (Table 2's e = 2 and 5):
+    # ASCII reads encoded inside the filter kernel (gk_filter_ascii) against
+    # the encoder pass followed by gk_filter
+    device_encoded = {}
+    for e in (0, 2, 5):
+        def sep(e=e):
+            gk.gk_encode(asc, w.n_reads, w.stride, fixed_len=m, stride_words=sw, packed=packed, nflag=nflag,
+                         stream=stream)
+            gk.gk_filter(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, e, accept=accept,
+                         edits=edits, stream=stream)
+
+        def fused(e=e):
+            gk.gk_filter_ascii(ref, asc, w.stride, w.n_reads, m, pairs.pair_read, pairs.pair_off, e, accept=accept,
+                               edits=edits, stream=stream)
+
+        for f in (sep, fused, sep, fused):
+            f()
+        device_encoded[f"e{e}"] = {
+            "fused_gpairs_s": w.n_pairs / (time_events(torch, fused, 20, stream) * 1e-3) / 1e9,
+            "encode_then_filter_gpairs_s": w.n_pairs / (time_events(torch, sep, 20, stream) * 1e-3) / 1e9}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world)
@@ -413,6 +434,7 @@ def run_mine(args):
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "device_encoded_one_threshold": device_encoded,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -159,6 +159,31 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
               int count_mode, uint32_t flags, uint8_t *accept_out,
               uint16_t *edits_out, uint32_t *err_count, void *stream);
 
+/*
+ * gk_filter_ascii -- gk_filter on reads given as ASCII rows, encoded inside
+ * the filter kernel (the paper's device-encoded mode, Sec. 3.3, without a
+ * separate encoding pass or a packed copy of the reads).  The warp encodes
+ * each distinct read among its 32 pairs once (runs of one read id), so
+ * candidates of a read should sit side by side; any order is correct.
+ * Same results as gk_encode + gk_filter on the same reads.
+ *
+ * Arguments as gk_filter, except:
+ *   ascii        device, n_reads rows of ascii_stride bytes (read i at
+ *                ascii + i*ascii_stride); only the first m bytes of a row are
+ *                read; a byte other than A/C/G/T (either case) makes the
+ *                read undefined (Sec. 3.3)
+ *   ascii_stride bytes between rows, >= m (rows on 4-byte boundaries are
+ *                loaded 4 bytes at a time)
+ * Errors as gk_filter (GK_EINVAL for a null ascii with m > 0 or a stride
+ * below m).
+ */
+int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride,
+                    uint64_t n_reads, uint32_t m, const uint32_t *pair_read,
+                    const uint32_t *pair_off, const uint8_t *pair_e,
+                    uint32_t fixed_e, uint64_t n_pairs, int count_mode,
+                    uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
+                    uint32_t *err_count, void *stream);
+
 /* Tiling of the batched filter (chosen by the autotuner). */
 typedef struct {
   uint32_t words_per_thread; /* words of a pair held per lane: 2, 3, 4, 6 or 8;

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "batched.cuh"
+#include "filter_ascii.cuh"
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -17,6 +18,8 @@ cudaError_t launch_filter_w1_4(int W, int variant, const FilterArgs &a, cudaStre
 cudaError_t launch_filter_w5_8(int W, int variant, const FilterArgs &a, cudaStream_t stream);
 cudaError_t launch_filter_w9_12(int W, int variant, const FilterArgs &a, cudaStream_t stream);
 cudaError_t launch_filter_w13_16(int W, int variant, const FilterArgs &a, cudaStream_t stream);
+cudaError_t launch_filter_ascii_w1_8(int W, int variant, const AsciiArgs &g, cudaStream_t stream);
+cudaError_t launch_filter_ascii_w9_16(int W, int variant, const AsciiArgs &g, cudaStream_t stream);
 
 namespace {
 thread_local std::string t_last_error;
@@ -34,7 +37,9 @@ int cuda_check(cudaError_t err, const char *what) {
   return fail(GK_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
 }
 
-cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
+// Variant of the per-pair code for a launch: 2 deferred erosion, 1 exact
+// with every shift below 32, 0 exact for any thresholds.
+int filter_variant(const FilterArgs &a) {
   // Every shift count below 32 (one threshold under 32, or reads of at most
   // 32 bases): the edge vectors live in the end words only.
   const bool small = (!a.pair_e && a.fixed_e < 32) || a.m <= 32;
@@ -42,7 +47,11 @@ cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
   // (e >= 2) to repay its once-per-pair corrections (measured on GB300: from
   // e = 2 it is as fast or faster at 100-300 bp).
   const bool deferred = a.edge_on && !a.pair_e && a.fixed_e >= 2 && (a.fixed_e <= 30 || a.m <= 31);
-  const int variant = deferred ? 2 : (small ? 1 : 0);
+  return deferred ? 2 : (small ? 1 : 0);
+}
+
+cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
+  const int variant = filter_variant(a);
   if (W >= 1 && W <= 4) return launch_filter_w1_4(W, variant, a, stream);
   if (W <= 8) return launch_filter_w5_8(W, variant, a, stream);
   if (W <= 12) return launch_filter_w9_12(W, variant, a, stream);
@@ -262,6 +271,57 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 &&
                (pair_e || (n_dense && fixed_e >= e_queue))) ? 1 : 0;
   return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
+}
+
+int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride, uint64_t n_reads, uint32_t m,
+                    const uint32_t *pair_read, const uint32_t *pair_off, const uint8_t *pair_e, uint32_t fixed_e,
+                    uint64_t n_pairs, int count_mode, uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
+                    uint32_t *err_count, void *stream) {
+  gk::clear_error();
+  if (!ref) return fail(GK_EINVAL, "gk_filter_ascii: null reference handle");
+  if (m > GK_MAX_LEN) return fail(GK_ERANGE, "gk_filter_ascii: m above GK_MAX_LEN");
+  if (n_pairs == 0) return GK_OK;
+  if (n_pairs > kMaxPairs) return fail(GK_ERANGE, "gk_filter_ascii: too many pairs for one launch");
+  const bool result_byte = (flags & GK_FLAG_RESULT_BYTE) != 0;
+  if (!pair_read || !pair_off || !accept_out || (!edits_out && !result_byte))
+    return fail(GK_EINVAL, "gk_filter_ascii: null pair or output buffer");
+  if (m > 0 && (!ascii || ascii_stride < m))
+    return fail(GK_EINVAL, "gk_filter_ascii: ascii missing or ascii_stride < m");
+  if (!pair_e && fixed_e > 255) return fail(GK_ERANGE, "gk_filter_ascii: fixed_e above 255");
+  if (result_byte && pair_e)
+    return fail(GK_EINVAL, "gk_filter_ascii: GK_FLAG_RESULT_BYTE needs one threshold (pair_e NULL)");
+  if (result_byte && fixed_e > 252)
+    return fail(GK_ERANGE, "gk_filter_ascii: GK_FLAG_RESULT_BYTE needs fixed_e <= 252");
+  if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
+    return fail(GK_EINVAL, "gk_filter_ascii: unknown count_mode");
+  if (flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE))
+    return fail(GK_EINVAL, "gk_filter_ascii: unknown flags");
+  gk::AsciiArgs g{};
+  gk::FilterArgs &a = g.f;
+  a.ref_hl = ref->hl;
+  a.ref_nidx = ref->nidx;
+  a.ref_len = ref->n_bases;
+  a.n_reads = n_reads;
+  a.m = m;
+  a.pair_read = pair_read;
+  a.pair_off = pair_off;
+  a.pair_e = pair_e;
+  a.fixed_e = fixed_e;
+  a.n_pairs = n_pairs;
+  a.count_mode = count_mode;
+  a.edge_on = (flags & GK_FLAG_NO_EDGE_FIX) ? 0 : 1;
+  a.result_byte = result_byte ? 1 : 0;
+  a.accept = accept_out;
+  a.edits = edits_out;
+  a.err_count = err_count;
+  g.ascii = ascii;
+  g.ascii_stride = ascii_stride;
+  g.rows_aligned = (aligned(ascii, 4) && ascii_stride % 4 == 0) ? 1 : 0;
+  const int W = m == 0 ? 1 : (int)((m + 31) / 32);
+  const int variant = gk::filter_variant(a);
+  const cudaError_t err = W <= 8 ? gk::launch_filter_ascii_w1_8(W, variant, g, (cudaStream_t)stream)
+                                 : gk::launch_filter_ascii_w9_16(W, variant, g, (cudaStream_t)stream);
+  return gk::cuda_check(err, "gk_filter_ascii: launch");
 }
 
 uint64_t gk_filter_batched_workspace(uint64_t n_pairs) { return gk::batch_scratch_bytes(n_pairs); }

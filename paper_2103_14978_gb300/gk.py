@@ -49,6 +49,9 @@ _SIGS = {
     "gk_filter": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_uint32,
                    _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
                    _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_ascii": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_void_p,
+                         _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int, _c.c_uint32, _c.c_void_p,
+                         _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_probe_alu": ([_c.c_int, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_filter_batched_workspace": ([_c.c_uint64], _c.c_uint64),
     "gk_filter_batched": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_void_p,
@@ -245,6 +248,36 @@ def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: i
         ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
         _dptr(read_nflag, torch.uint8, "read_nflag", n_reads), m,
         _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n),
+        pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
+        None if result_byte else _dptr(edits, torch.int16, "edits", n),
+        _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    return accept, (None if result_byte else edits)
+
+
+def gk_filter_ascii(ref: Reference, ascii: torch.Tensor, ascii_stride: int, n_reads: int, m: int,
+                    pair_read: torch.Tensor, pair_off: torch.Tensor, e, count_mode: int = GK_COUNT_RUNS4,
+                    flags: int = 0, accept: torch.Tensor | None = None, edits: torch.Tensor | None = None,
+                    err_count: torch.Tensor | None = None, stream=None):
+    """Filter pairs whose reads are ASCII rows on the device, encoding them in
+    the filter kernel (gk_filter_ascii).  Same arguments and results as
+    gk_filter, with the uint8 CUDA tensor ``ascii`` (n_reads rows of
+    ascii_stride bytes) in place of the packed reads."""
+    n = pair_read.numel()
+    dev = pair_read.device
+    result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
+    if accept is None:
+        accept = torch.empty(n, dtype=torch.uint8, device=dev)
+    if edits is None and not result_byte:
+        edits = torch.empty(n, dtype=torch.int16, device=dev)
+    pe = None
+    fixed_e = 0
+    if isinstance(e, torch.Tensor):
+        pe = _dptr(e, torch.uint8, "e", n)
+    else:
+        fixed_e = int(e)
+    _check(lib().gk_filter_ascii(
+        ref.handle, _dptr(ascii, torch.uint8, "ascii", n_reads * ascii_stride if m > 0 else 0), ascii_stride,
+        n_reads, m, _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n),
         pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
         None if result_byte else _dptr(edits, torch.int16, "edits", n),
         _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
