@@ -471,8 +471,8 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
             tickets.append(pipe.submit(h_asc, w.n_reads, h_pr, h_po, acc, ed))
         pipe.wait(tickets[-1])
 
-    run(2)
-    steps = max(3, min(args.steps, 20))
+    run(2 * slots)  # every slot's buffers used once before the timed region
+    steps = max(3, min(args.steps, 30))
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
