@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -103,7 +104,7 @@ class ClockSampler:
     def __init__(self, uuid: str | None):
         self.proc = None
         self.uuid = uuid
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gk_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

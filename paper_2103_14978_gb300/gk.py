@@ -103,7 +103,7 @@ def lib() -> ctypes.CDLL:
             if not os.path.exists(LIB_PATH):
                 raise RuntimeError(
                     f"{LIB_PATH} is missing: build it with "
-                    "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+                    "`python -m paper_2103_14978_gb300.build` (no CPU fallback exists)")
             L = ctypes.CDLL(LIB_PATH)
             for name, (args, res) in _SIGS.items():
                 fn = getattr(L, name)
