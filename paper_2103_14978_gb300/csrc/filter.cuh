@@ -30,6 +30,8 @@
 // GateKeeper) such masks are the window compared with code 00, ANDed once.
 #pragma once
 
+#include <atomic>
+
 #include "gk_internal.cuh"
 
 namespace gk {
@@ -757,26 +759,32 @@ cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
     return cudaGetLastError();
   }
   // Persistent warps: a few waves of resident blocks.  The dynamic shared
-  // memory limit and the occupancy are set up once per device.
+  // memory limit and the occupancy are set up once per device (threads that
+  // race here repeat the same idempotent setup; the block count is
+  // published after the SM count).
   constexpr int kMaxDev = 64;
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-  static int per_sm[kMaxDev] = {}, sms[kMaxDev] = {};
+  static std::atomic<int> per_sm[kMaxDev], sms[kMaxDev];
   const size_t smem = compact_smem_bytes<W>();
-  if (per_sm[dev] == 0) {
+  int blocks_per_sm = per_sm[dev].load(std::memory_order_acquire);
+  if (blocks_per_sm == 0) {
     err = cudaFuncSetAttribute(filter_kernel<W, VARIANT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    int count = 0;
+    err = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     int n = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, filter_kernel<W, VARIANT, true>, kFilterThreads, smem);
     if (err != cudaSuccess) return err;
-    per_sm[dev] = n < 1 ? 1 : n;
+    blocks_per_sm = n < 1 ? 1 : n;
+    sms[dev].store(count, std::memory_order_relaxed);
+    per_sm[dev].store(blocks_per_sm, std::memory_order_release);
   }
-  const uint64_t wave = 4ull * (uint64_t)sms[dev] * (uint64_t)per_sm[dev];
+  const uint64_t wave = 4ull * (uint64_t)sms[dev].load(std::memory_order_relaxed) * (uint64_t)blocks_per_sm;
   if (blocks > wave) blocks = (unsigned)wave;
   filter_kernel<W, VARIANT, true><<<blocks, kFilterThreads, smem, stream>>>(a);
   return cudaGetLastError();

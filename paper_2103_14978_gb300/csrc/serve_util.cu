@@ -2,6 +2,8 @@
 // the pairs of many requests, whose read ids are relative to each request's
 // own reads; this kernel moves them to the positions the reads were given in
 // the launch's read buffer.
+#include <atomic>
+
 #include "gk_internal.cuh"
 
 namespace {
@@ -119,12 +121,19 @@ extern "C" int gk_gather(const uint64_t *dst, const uint64_t *src, const uint64_
   if (n == 0) return GK_OK;
   if (!dst || !src || !bytes) return gk::fail(GK_EINVAL, "gk_gather: null table");
   if (n > 0x7fffffffu) return gk::fail(GK_ERANGE, "gk_gather: too many entries");
-  static int sms = 0;
+  // SM count of the current device, looked up once per device.
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> sm_count[kMaxDev];
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return gk::cuda_check(err, "gk_gather: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDev) return gk::fail(GK_ERANGE, "gk_gather: device index too large");
+  int sms = sm_count[dev].load(std::memory_order_relaxed);
   if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess || sms < 1)
-      sms = 132;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return gk::cuda_check(err, "gk_gather: cudaDeviceGetAttribute");
+    if (sms < 1) sms = 1;
+    sm_count[dev].store(sms, std::memory_order_relaxed);
   }
   const uint32_t grid = n < 2u * (uint32_t)sms ? n : 2u * (uint32_t)sms;
   gather_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(dst, src, bytes, n);
