@@ -378,6 +378,46 @@ def run_mine(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     probe = probe_alu(torch, gk, stream, args.probe_all)
 
+    # The bit-sliced form of the same step: the batch sliced once (32 pairs per
+    # word, position-major), then one gk_filter_sliced per threshold.
+    sliced = None
+    if all(gk.sliced_supported(m, e) for e in E_SWEEP):
+        sbuf = torch.empty(gk.gk_sliced_bytes(w.n_pairs, m), dtype=torch.uint8, device=dev)
+
+        def step_sliced(ev=None):
+            gk.gk_encode(asc, w.n_reads, w.stride, fixed_len=m, stride_words=sw, packed=packed, nflag=nflag,
+                         stream=stream)
+            if ev is not None:
+                ev[0][0].record(stream)
+            gk.gk_slice(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, out=sbuf,
+                        stream=stream)
+            if ev is not None:
+                ev[0][1].record(stream)
+            for i, e in enumerate(E_SWEEP):
+                if ev is not None:
+                    ev[i + 1][0].record(stream)
+                gk.gk_filter_sliced(sbuf, w.n_pairs, m, e, accept=accept, edits=edits, stream=stream)
+                if ev is not None:
+                    ev[i + 1][1].record(stream)
+
+        for _ in range(args.warmup):
+            step_sliced()
+        sev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                for _ in range(len(E_SWEEP) + 1)] for _ in range(args.steps)]
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for k in range(args.steps):
+            step_sliced(sev[k])
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1) / args.steps
+        seg = [statistics.mean(sev[k][i][0].elapsed_time(sev[k][i][1]) for k in range(args.steps))
+               for i in range(len(E_SWEEP) + 1)]
+        sliced = {"gpairs_s": pairs_per_step / (sms * 1e-3) / 1e9, "ms_per_step": sms, "slice_ms": seg[0],
+                  "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, seg[1:])}}
+        del sbuf
+
     # the paper's device-encoded mode at one threshold (Table 2's e = 2 and 5):
     # ASCII reads encoded inside the filter kernel (gk_filter_ascii) against
     # the encoder pass followed by gk_filter
@@ -437,6 +477,7 @@ def run_mine(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "device_encoded_one_threshold": device_encoded,
+        "sliced_step": sliced,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -184,6 +184,59 @@ int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride,
                     uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
                     uint32_t *err_count, void *stream);
 
+/*
+ * Bit-sliced batches: the same filter (Sec. 2.1, Sec. 3.3, Sec. 3.4) for a
+ * batch filtered at several thresholds, as in the paper's threshold sweeps
+ * (Sec. 4).  gk_slice gathers every pair's read and genome window once and
+ * stores them position-major, 32 pairs per 32-bit word (one word per base
+ * position and bit plane); each gk_filter_sliced call then filters the whole
+ * batch at one threshold from that buffer.  Results equal gk_filter's with
+ * the edge OR on (flags without GK_FLAG_NO_EDGE_FIX), bit for bit.
+ * Limits: 1 <= m <= GK_SLICED_MAX_LEN, min(e, m-1) <= GK_SLICED_MAX_SHIFT.
+ */
+#define GK_SLICED_MAX_LEN 255u
+#define GK_SLICED_MAX_SHIFT 10u
+
+/* Bytes of the sliced buffer of n_pairs pairs of read length m:
+ * (2m + 1) * 8 * (ceil(n_pairs/32) rounded up to 32); 0 when n_pairs is 0 or
+ * m is outside 1..GK_SLICED_MAX_LEN. */
+uint64_t gk_sliced_bytes(uint64_t n_pairs, uint32_t m);
+
+/*
+ * gk_slice -- fill a sliced buffer from the pairs (arguments as gk_filter).
+ *   sliced       device, caller-owned, 16-byte aligned, sliced_cap bytes
+ *                (at least gk_sliced_bytes(n_pairs, m)); holds the batch
+ *                until overwritten
+ *   err_count    device uint32 or NULL: incremented once per invalid pair
+ * Each pair's status is decided here: invalid (read id >= n_reads or
+ * off + m > reference length) and undefined (a non-ACGT base in the read or
+ * the window) pairs get their fixed results from every gk_filter_sliced.
+ * Asynchronous on `stream`; GK_EINVAL / GK_ERANGE before any work for bad
+ * arguments.
+ */
+int gk_slice(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
+             uint64_t n_reads, const uint8_t *read_nflag, uint32_t m,
+             const uint32_t *pair_read, const uint32_t *pair_off,
+             uint64_t n_pairs, void *sliced, uint64_t sliced_cap,
+             uint32_t *err_count, void *stream);
+
+/*
+ * gk_filter_sliced -- filter a sliced batch at threshold fixed_e.
+ *   sliced, sliced_cap  a buffer filled by gk_slice with the same n_pairs
+ *                       and m (not checked beyond its size)
+ *   fixed_e             0..255; min(fixed_e, m-1) <= GK_SLICED_MAX_SHIFT
+ *   count_mode          GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT
+ *   flags               0 or GK_FLAG_RESULT_BYTE (fixed_e <= 252);
+ *                       GK_FLAG_NO_EDGE_FIX is GK_EINVAL
+ *   accept_out, edits_out  as gk_filter (16-byte aligned buffers take
+ *                       vector stores)
+ * Asynchronous on `stream`.
+ */
+int gk_filter_sliced(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs,
+                     uint32_t m, uint32_t fixed_e, int count_mode,
+                     uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
+                     void *stream);
+
 /* Tiling of the batched filter (chosen by the autotuner). */
 typedef struct {
   uint32_t words_per_thread; /* words of a pair held per lane: 2, 3, 4, 6 or 8;

@@ -52,6 +52,11 @@ _SIGS = {
     "gk_filter_ascii": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_void_p,
                          _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int, _c.c_uint32, _c.c_void_p,
                          _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_sliced_bytes": ([_c.c_uint64, _c.c_uint32], _c.c_uint64),
+    "gk_slice": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_uint32, _c.c_void_p,
+                  _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_sliced": ([_c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_uint32, _c.c_int, _c.c_uint32,
+                          _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_probe_alu": ([_c.c_int, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_filter_batched_workspace": ([_c.c_uint64], _c.c_uint64),
     "gk_filter_batched": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_void_p,
@@ -74,6 +79,8 @@ _SIGS = {
 }
 
 GK_NOALLOC_MAX_PAIRS = 1_000_000
+GK_SLICED_MAX_LEN = 255
+GK_SLICED_MAX_SHIFT = 10
 GK_GATHER_MAX_BYTES = 65536
 
 
@@ -281,6 +288,54 @@ def gk_filter_ascii(ref: Reference, ascii: torch.Tensor, ascii_stride: int, n_re
         pe, fixed_e, n, count_mode, flags, _dptr(accept, torch.uint8, "accept", n),
         None if result_byte else _dptr(edits, torch.int16, "edits", n),
         _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    return accept, (None if result_byte else edits)
+
+
+def sliced_supported(m: int, e: int) -> bool:
+    """Whether gk_filter_sliced filters read length m at threshold e."""
+    return 1 <= m <= GK_SLICED_MAX_LEN and min(int(e), m - 1) <= GK_SLICED_MAX_SHIFT
+
+
+def gk_sliced_bytes(n_pairs: int, m: int) -> int:
+    return int(lib().gk_sliced_bytes(n_pairs, m))
+
+
+def gk_slice(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: int,
+             read_nflag: torch.Tensor | None, m: int, pair_read: torch.Tensor, pair_off: torch.Tensor,
+             out: torch.Tensor | None = None, err_count: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Gather and transpose a batch of pairs into a sliced buffer (gk_slice);
+    returns the buffer (a uint8 CUDA tensor, ``out`` when given)."""
+    n = pair_read.numel()
+    nbytes = gk_sliced_bytes(n, m) if n else 0
+    if out is None:
+        out = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=pair_read.device)
+    if reads.numel() < n_reads * stride_words * 2:
+        raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
+    _check(lib().gk_slice(
+        ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
+        _dptr(read_nflag, torch.uint8, "read_nflag", n_reads), m,
+        _dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_off, torch.int32, "pair_off", n), n,
+        _dptr(out, torch.uint8, "out", nbytes), out.numel(), _dptr(err_count, torch.int32, "err_count", 1),
+        _stream(stream)))
+    return out
+
+
+def gk_filter_sliced(sliced: torch.Tensor, n_pairs: int, m: int, e: int, count_mode: int = GK_COUNT_RUNS4,
+                     flags: int = 0, accept: torch.Tensor | None = None, edits: torch.Tensor | None = None,
+                     stream=None):
+    """Filter a sliced batch at threshold ``e`` (gk_filter_sliced).  Returns
+    (accept uint8, edits int16 read as uint16), or (result bytes, None) with
+    GK_FLAG_RESULT_BYTE, as gk_filter."""
+    dev = sliced.device
+    result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
+    if accept is None:
+        accept = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
+    if edits is None and not result_byte:
+        edits = torch.empty(n_pairs, dtype=torch.int16, device=dev)
+    _check(lib().gk_filter_sliced(
+        _dptr(sliced, torch.uint8, "sliced"), sliced.numel(), n_pairs, m, int(e), count_mode, flags,
+        _dptr(accept, torch.uint8, "accept", n_pairs),
+        None if result_byte else _dptr(edits, torch.int16, "edits", n_pairs), _stream(stream)))
     return accept, (None if result_byte else edits)
 
 
