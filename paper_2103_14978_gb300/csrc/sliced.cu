@@ -6,37 +6,209 @@
 namespace gk {
 namespace {
 
-// One thread per group of 32 pairs.  The block's 4096 pair ids are read
-// coalesced into shared memory (rows of 33 words: conflict-free per-thread
-// reads), then every thread gathers and transposes its group.
+constexpr int kSliceTpg = 4;                   // lanes per group
+constexpr int kSliceRows = 32 / kSliceTpg;     // pairs (matrix rows) per lane
+constexpr int kSliceGroups = kSliceThreads / kSliceTpg;
+
+// Transposes a 32x32 bit matrix held by the kSliceTpg consecutive lanes of
+// a group, kSliceRows rows each (lane part p: rows 8p .. 8p+7 in v[]; bit b
+// of a row = column b).  Afterwards part p holds columns 8p .. 8p+7 (bit j =
+// row j).  Recursive block swap as in a one-thread transpose: the 16- and
+// 8-row stages pair rows held by different lanes (a shuffle and a byte
+// permute per row, the selector picking the lane's half), the 4-, 2- and
+// 1-row stages run in registers.
+__device__ __forceinline__ void transpose_rows(uint32_t (&v)[kSliceRows], uint32_t part) {
+#pragma unroll
+  for (int k = 16; k >= kSliceRows; k >>= 1) {
+    const int d = k / kSliceRows;  // lane distance of rows i and i+k
+    const bool up = (part & (uint32_t)d) != 0;
+    const uint32_t sel = k == 16 ? (up ? 0x3276u : 0x5410u) : (up ? 0x3715u : 0x6240u);
+#pragma unroll
+    for (int i = 0; i < kSliceRows; ++i) v[i] = __byte_perm(v[i], __shfl_xor_sync(0xffffffffu, v[i], d), sel);
+  }
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const int S = 4 >> st;
+    const uint32_t M = st == 0 ? 0x0F0F0F0Fu : (st == 1 ? 0x33333333u : 0x55555555u);
+#pragma unroll
+    for (int i = 0; i < kSliceRows; ++i) {
+      if (i & S) continue;
+      const uint32_t x = v[i], y = v[i + S];
+      v[i] = (x & M) | ((y << S) & ~M);
+      v[i + S] = ((x >> S) & M) | (y & ~M);
+    }
+  }
+}
+
+// Stores the transposed word of positions 32w + 8p .. 32w + 8p + 7 (those
+// below m) into plane rows (h, l) of group g.
+__device__ __forceinline__ void store_rows(uint2 *plane, uint64_t pitch, uint64_t g, uint32_t q0, uint32_t m,
+                                           const uint32_t (&h)[kSliceRows], const uint32_t (&l)[kSliceRows]) {
+#pragma unroll
+  for (int i = 0; i < kSliceRows; ++i)
+    if (q0 + i < m) __stcs(plane + (uint64_t)(q0 + i) * pitch + g, make_uint2(h[i], l[i]));
+}
+
+// Four lanes per group of 32 pairs, 8 pairs per lane.  The block's pair ids
+// come in coalesced through shared memory (rows of 33 words: the lanes'
+// reads hit distinct banks); each lane reads its 8 pairs' words two per
+// row at a time in 16-byte loads (a pair with the read of the pair before it
+// reuses that read's words), the group's four lanes transpose them, and the
+// planes are written with streaming stores, which leave the genome and the
+// reads in L2.
 __global__ void __launch_bounds__(kSliceThreads) slice_kernel(const SliceArgs a, uint32_t *err_count) {
-  __shared__ uint32_t s_rid[kSliceThreads * 33], s_off[kSliceThreads * 33];
-  const uint64_t g0 = (uint64_t)blockIdx.x * kSliceThreads;
-  for (int i = threadIdx.x; i < 32 * kSliceThreads; i += kSliceThreads) {
+  constexpr int R = kSliceRows;
+  __shared__ uint32_t s_rid[kSliceGroups * 33], s_off[kSliceGroups * 33];
+  const uint64_t groups = sliced_groups(a.n_pairs);
+  const uint64_t g0 = (uint64_t)blockIdx.x * kSliceGroups;
+  for (int i = threadIdx.x; i < 32 * kSliceGroups; i += kSliceThreads) {
     const uint64_t p = g0 * 32 + (uint64_t)i;
     uint32_t rid = 0xffffffffu, off = 0xffffffffu;
     if (p < a.n_pairs) {
-      rid = __ldg(a.pair_read + p);
-      off = __ldg(a.pair_off + p);
+      rid = ldro(a.pair_read + p);
+      off = ldro(a.pair_off + p);
     }
     s_rid[(i >> 5) * 33 + (i & 31)] = rid;
     s_off[(i >> 5) * 33 + (i & 31)] = off;
   }
   __syncthreads();
-  const uint64_t g = g0 + threadIdx.x;
-  if (g >= sliced_groups(a.n_pairs)) return;
-  const uint64_t left = a.n_pairs - g * 32;
-  const uint32_t n_here = left < 32 ? (uint32_t)left : 32u;
-  const uint32_t n_inv = slice_group(a, g, s_rid + threadIdx.x * 33, s_off + threadIdx.x * 33, 1, n_here);
-  if (n_inv && err_count) atomicAdd(err_count, n_inv);
+  const uint32_t gl = threadIdx.x / kSliceTpg, part = threadIdx.x % kSliceTpg;
+  const uint64_t g = g0 + gl;  // a group past the end runs on zeros (its lanes shuffle) and stores nothing
+  const bool live = g < groups;
+  const uint32_t *rid = s_rid + gl * 33 + part * R, *off = s_off + gl * 33 + part * R;
+  const uint64_t first = g * 32 + part * R;
+  const uint32_t n_here = first >= a.n_pairs ? 0u : (uint32_t)min_u64(R, a.n_pairs - first);
+
+  // Status per pair: invalid (read id or window out of range), undefined (a
+  // non-ACGT base in the read, from its flag, or in the window, from the
+  // genome's N index, Sec. 3.3).  A pair with the previous pair's read
+  // reuses that read's flag (and, below, its words).
+  uint32_t und = 0, inv = 0, ok = 0, same = 0, prev = 0xffffffffu, prev_nf = 0;  // local bits j < R
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    if ((uint32_t)j >= n_here) continue;
+    const uint32_t r = rid[j], o = off[j];
+    if ((uint64_t)r >= a.n_reads || (uint64_t)o + a.m > a.ref_len) {
+      inv |= 1u << j;
+      prev = 0xffffffffu;
+      continue;
+    }
+    ok |= 1u << j;
+    uint32_t nf;
+    if (r == prev) {
+      same |= 1u << j;
+      nf = prev_nf;
+    } else {
+      nf = a.read_nflag ? (uint32_t)ldro(a.read_nflag + r) : 0u;
+    }
+    prev = r;
+    prev_nf = nf;
+    bool u = nf != 0;
+    if (a.ref_nidx) {
+      const uint2 ni = ldro(a.ref_nidx + (o >> 5));
+      const uint32_t q = ni.x >> (o & 31);
+      const uint64_t first = q ? (uint64_t)o + (uint32_t)(__ffs(q) - 1) : (uint64_t)ni.y;
+      u = u || first < (uint64_t)o + a.m;
+    }
+    if (u) und |= 1u << j;
+  }
+  if (inv && err_count) atomicAdd(err_count, popc32(inv));
+  uint32_t gund = und << (part * R), ginv = inv << (part * R);
+#pragma unroll
+  for (int d = 1; d < kSliceTpg; d <<= 1) {
+    gund |= __shfl_xor_sync(0xffffffffu, gund, d);
+    ginv |= __shfl_xor_sync(0xffffffffu, ginv, d);
+  }
+  if (live && part == 0) a.st[g] = make_uint2(gund, ginv);
+
+  const uint32_t m = a.m, W = (m + 31) / 32;
+  const bool wide = (a.stride_words & 1u) == 0 && (reinterpret_cast<uintptr_t>(a.reads) & 15u) == 0;
+  for (uint32_t w = 0; w < W; w += 2) {
+    const bool two = w + 1 < W;
+    uint32_t h0[R], l0[R], h1[R], l1[R];
+    {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (((ok & ~same) >> j) & 1u) {
+          const uint2 *row = a.reads + (uint64_t)rid[j] * a.stride_words + w;
+          if (wide) {
+            v = ldro(reinterpret_cast<const uint4 *>(row));
+          } else {
+            const uint2 x = ldro(row), y = two ? ldro(row + 1) : make_uint2(0u, 0u);
+            v = make_uint4(x.x, x.y, y.x, y.y);
+          }
+        } else if (!((same >> j) & 1u)) {
+          v = make_uint4(0u, 0u, 0u, 0u);
+        }
+        h0[j] = v.x;
+        l0[j] = v.y;
+        h1[j] = v.z;
+        l1[j] = v.w;
+      }
+    }
+    const uint32_t q0 = 32 * w + part * R;
+    transpose_rows(h0, part);
+    transpose_rows(l0, part);
+    if (live) store_rows(a.rs, a.pitch, g, q0, m, h0, l0);
+    if (two) {  // warp-uniform
+      transpose_rows(h1, part);
+      transpose_rows(l1, part);
+      if (live) store_rows(a.rs, a.pitch, g, q0 + 32, m, h1, l1);
+    }
+    // Window words w, w+1: genome words t, t+1, t+2 (t = off/32 + w) from
+    // the aligned 16-byte loads at the even word at or below t; the last word
+    // read is at most off/32 + W + 1 <= n_words + 1, inside the genome's two
+    // zero tail words.
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      uint32_t a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+      if ((ok >> j) & 1u) {
+        const uint32_t o = off[j];
+        const uint32_t t = (o >> 5) + w;
+        const uint4 *gq = reinterpret_cast<const uint4 *>(a.ref_hl + (t & ~1u));
+        const uint4 A = ldro(gq);
+        uint2 x0, x1, x2 = make_uint2(0u, 0u);
+        if ((t & 1u) == 0) {
+          x0 = make_uint2(A.x, A.y);
+          x1 = make_uint2(A.z, A.w);
+          if (two) {
+            const uint4 B = ldro(gq + 1);
+            x2 = make_uint2(B.x, B.y);
+          }
+        } else {
+          const uint4 B = ldro(gq + 1);
+          x0 = make_uint2(A.z, A.w);
+          x1 = make_uint2(B.x, B.y);
+          x2 = make_uint2(B.z, B.w);
+        }
+        const uint32_t sh = o & 31;
+        a0 = __funnelshift_r(x0.x, x1.x, sh);
+        b0 = __funnelshift_r(x0.y, x1.y, sh);
+        a1 = __funnelshift_r(x1.x, x2.x, sh);
+        b1 = __funnelshift_r(x1.y, x2.y, sh);
+      }
+      h0[j] = a0;
+      l0[j] = b0;
+      h1[j] = a1;
+      l1[j] = b1;
+    }
+    transpose_rows(h0, part);
+    transpose_rows(l0, part);
+    if (live) store_rows(a.gs, a.pitch, g, q0, m, h0, l0);
+    if (two) {
+      transpose_rows(h1, part);
+      transpose_rows(l1, part);
+      if (live) store_rows(a.gs, a.pitch, g, q0 + 32, m, h1, l1);
+    }
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_slice(const SliceArgs &a, uint32_t *err_count, cudaStream_t stream) {
-  const uint64_t groups = sliced_groups(a.n_pairs);
-  const unsigned blocks = (unsigned)((groups + kSliceThreads - 1) / kSliceThreads);
-  slice_kernel<<<blocks, kSliceThreads, 0, stream>>>(a, err_count);
+  const uint64_t blocks = (sliced_groups(a.n_pairs) + kSliceGroups - 1) / kSliceGroups;
+  slice_kernel<<<(unsigned)blocks, kSliceThreads, 0, stream>>>(a, err_count);
   return cudaGetLastError();
 }
 
@@ -97,8 +269,8 @@ int gk_slice(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64_
   a.n_pairs = n_pairs;
   a.pitch = gk::sliced_pitch(n_pairs);
   a.rs = reinterpret_cast<uint2 *>(sliced);
-  a.gs = a.rs + (uint64_t)m * a.pitch;
-  a.st = a.gs + (uint64_t)m * a.pitch;
+  a.gs = a.rs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
+  a.st = a.gs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
   return gk::cuda_check(gk::launch_slice(a, err_count, (cudaStream_t)stream), "gk_slice: launch");
 }
 
@@ -125,8 +297,8 @@ int gk_filter_sliced(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs, 
   gk::SlicedArgs a{};
   a.pitch = gk::sliced_pitch(n_pairs);
   a.rs = reinterpret_cast<const uint2 *>(sliced);
-  a.gs = a.rs + (uint64_t)m * a.pitch;
-  a.st = a.gs + (uint64_t)m * a.pitch;
+  a.gs = a.rs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
+  a.st = a.gs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
   a.n_pairs = n_pairs;
   a.m = m;
   a.e = fixed_e;

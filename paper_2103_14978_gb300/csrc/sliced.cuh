@@ -34,7 +34,9 @@
 //   rs[q * pitch + g]   read position q of group g, q < m
 //   gs[q * pitch + g]   window position q of group g, q < m
 //   st[g]               {undefined pairs, invalid pairs} of group g
-// in one buffer: rs, then gs, then st; (2m + 1) * pitch * 8 bytes.
+// in one buffer: rs and gs each with kSlicedPad rows past m (never
+// written; the filter's prefetch reads them and discards what it reads),
+// then st; (2(m + kSlicedPad) + 1) * pitch * 8 bytes.
 #pragma once
 
 #include "gk_internal.cuh"
@@ -45,13 +47,14 @@ constexpr int kSliceThreads = 128;   // slice: one thread per group
 constexpr int kSlicedThreads = 128;  // filter: one thread per group
 constexpr int kSlicedMaxK = (int)GK_SLICED_MAX_SHIFT;  // largest shift count with a compiled filter
 constexpr uint32_t kSlicedMaxLen = GK_SLICED_MAX_LEN;
+constexpr uint32_t kSlicedPad = 16;  // rows past m: the ring's prefetch reads up to m - 1 + (L - K - 1)
 
 __host__ __device__ __forceinline__ uint64_t sliced_groups(uint64_t n_pairs) { return (n_pairs + 31) / 32; }
 __host__ __device__ __forceinline__ uint64_t sliced_pitch(uint64_t n_pairs) {
   return (sliced_groups(n_pairs) + 31) / 32 * 32;
 }
 __host__ __device__ __forceinline__ uint64_t sliced_bytes(uint64_t n_pairs, uint32_t m) {
-  return (2ull * m + 1) * sliced_pitch(n_pairs) * 8ull;
+  return (2ull * (m + kSlicedPad) + 1) * sliced_pitch(n_pairs) * 8ull;
 }
 
 // ---- portable forms of the few intrinsics (host: a CPU check of this code) ----
@@ -124,37 +127,6 @@ __host__ __device__ __forceinline__ T ldro(const T *p) {
 #endif
 }
 
-// 32x32 bit transpose in place: afterwards bit j of a[i] is what bit i of
-// a[j] was.  Recursive block swap: the off-diagonal 16x16 blocks, then 8x8,
-// 4x4, 2x2 and 1x1 blocks inside every block (byte permutes for 16 and 8).
-__host__ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const uint32_t x = a[k], y = a[k + 16];
-    a[k] = bperm(x, y, 0x5410);
-    a[k + 16] = bperm(x, y, 0x7632);
-  }
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k & 8) continue;
-    const uint32_t x = a[k], y = a[k + 8];
-    a[k] = bperm(x, y, 0x6240);
-    a[k + 8] = bperm(x, y, 0x7351);
-  }
-#pragma unroll
-  for (int st = 0; st < 3; ++st) {
-    const int S = 4 >> st;
-    const uint32_t M = st == 0 ? 0x0F0F0F0Fu : (st == 1 ? 0x33333333u : 0x55555555u);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if (k & S) continue;
-      const uint32_t x = a[k], y = a[k + S];
-      a[k] = (x & M) | ((y << S) & ~M);
-      a[k + S] = ((x >> S) & M) | (y & ~M);
-    }
-  }
-}
-
 // ---- slice ----------------------------------------------------------------
 
 struct SliceArgs {
@@ -172,72 +144,6 @@ struct SliceArgs {
   uint64_t pitch;
   uint2 *rs, *gs, *st;
 };
-
-// Status of pair (rid, off): 2 invalid (read id or window out of range), 1
-// undefined (a non-ACGT base in the read or the window, Sec. 3.3), 0 filter.
-__host__ __device__ __forceinline__ int slice_status(const SliceArgs &a, uint32_t rid, uint32_t off) {
-  if ((uint64_t)rid >= a.n_reads || (uint64_t)off + a.m > a.ref_len) return 2;
-  if (a.read_nflag && ldro(a.read_nflag + rid)) return 1;
-  if (a.ref_nidx) {
-    const uint2 ni = ldro(a.ref_nidx + (off >> 5));
-    const uint32_t q = ni.x >> (off & 31);
-    const uint64_t first = q ? (uint64_t)off + (uint32_t)(ffs32(q) - 1) : (uint64_t)ni.y;
-    if (first < (uint64_t)off + a.m) return 1;
-  }
-  return 0;
-}
-
-// Slices group g: rid[j], off[j] are its pairs' ids (j < n_here).  Returns
-// the number of invalid pairs.
-__host__ __device__ __forceinline__ uint32_t slice_group(const SliceArgs &a, uint64_t g, const uint32_t *rid,
-                                                         const uint32_t *off, int stride, uint32_t n_here) {
-  uint32_t und = 0, inv = 0, ok = 0;
-  for (uint32_t j = 0; j < n_here; ++j) {
-    const int s = slice_status(a, rid[j * stride], off[j * stride]);
-    if (s == 2) inv |= 1u << j;
-    else ok |= 1u << j;  // in range: its words can be read
-    if (s == 1) und |= 1u << j;
-  }
-  a.st[g] = make_uint2(und, inv);
-  const uint32_t m = a.m, W = (m + 31) / 32;
-  for (uint32_t w = 0; w < W; ++w) {
-    uint32_t h[32], l[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      uint2 v = make_uint2(0u, 0u);
-      if ((ok >> j) & 1u) v = ldro(a.reads + (uint64_t)rid[j * stride] * a.stride_words + w);
-      h[j] = v.x;
-      l[j] = v.y;
-    }
-    transpose32(h);
-    transpose32(l);
-    uint2 *out = a.rs + (uint64_t)(32 * w) * a.pitch + g;
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (32 * w + i < m) out[(uint64_t)i * a.pitch] = make_uint2(h[i], l[i]);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      uint32_t hh = 0, ll = 0;
-      if ((ok >> j) & 1u) {
-        const uint32_t o = off[j * stride];
-        // window words off/32 + w and the next (the genome has two zero tail words)
-        const uint2 *gp = a.ref_hl + (o >> 5) + w;
-        const uint2 x = ldro(gp), y = ldro(gp + 1);
-        hh = fshr(x.x, y.x, o & 31);
-        ll = fshr(x.y, y.y, o & 31);
-      }
-      h[j] = hh;
-      l[j] = ll;
-    }
-    transpose32(h);
-    transpose32(l);
-    out = a.gs + (uint64_t)(32 * w) * a.pitch + g;
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (32 * w + i < m) out[(uint64_t)i * a.pitch] = make_uint2(h[i], l[i]);
-  }
-  return popc32(inv);
-}
 
 // ---- filter -----------------------------------------------------------------
 
@@ -361,20 +267,38 @@ __host__ __device__ __forceinline__ void sliced_group(const SlicedArgs &a, uint6
   uint32_t B[5] = {0u, 0u, 0u, 0u, 0u};                              // count / 8
   const uint32_t runs = a.runs4 ? 0xffffffffu : 0u;
 
+  // Positions q0 .. q0+L-1 with an end correction (q in 3..K+3, the low
+  // corrections at p = q-2 in 1..K+1, or q in m-K..m-1, the high ones): one
+  // bit per position, so the other positions pay one bit test.
+  auto corr_bits = [&](uint32_t q0) -> uint32_t {
+    auto range = [](int lo, int hi) -> uint32_t {
+      lo = lo < 0 ? 0 : lo;
+      hi = hi > 31 ? 31 : hi;
+      if (hi < lo) return 0u;
+      return (hi == 31 ? 0xffffffffu : ((2u << hi) - 1u)) & ~((1u << lo) - 1u);
+    };
+    return range(3 - (int)q0, K + 3 - (int)q0) | range((int)m - K - (int)q0, (int)m - 1 - (int)q0);
+  };
+  uint32_t cm = 0;
   // One position: q runs, j = q mod L is a constant after unrolling.
   auto step = [&](uint32_t q, int j) {
-    {  // read position q + K + D into the slot position q - K - 1 leaves
+    // Read position q + K + D into the slot position q - K - 1 leaves, and
+    // window position q + 7.  Past m the rows are padding: the shift counts
+    // whose launches wait on memory (K <= 3) skip those loads, the others
+    // read them unconditionally (the vacated flag masks the read; window
+    // positions past m-1 are never used).
+    {
       const int s = (j + K + D) % L;
       const bool in = q + K + D < m;
-      const uint2 vv = in ? ldro(rload) : z2;
+      const uint2 vv = (K > 3 || in) ? ldro(rload) : z2;
       rh[s] = vv.x;
       rl[s] = vv.y;
       rx[s] = in ? 0u : 0xffffffffu;
       rload += P;
     }
-    {  // window position q + 7
+    {
       const int s = (j + 7) % 8;
-      const uint2 vv = (q + 7 < m) ? ldro(gload) : z2;
+      const uint2 vv = (K > 3 || q + 7 < m) ? ldro(gload) : z2;
       wh[s] = vv.x;
       wl[s] = vv.y;
       gload += P;
@@ -394,9 +318,9 @@ __host__ __device__ __forceinline__ void sliced_group(const SlicedArgs &a, uint6
     uint32_t f = v & accn;
     v = aprev & accn;
     aprev = accn;
-    const int p = (int)q - 2;
-    if (p >= 1 && p <= K + 1) f &= ~clr[(p - 1) * clr_stride];
-    {
+    if ((cm >> j) & 1u) {  // an end correction at p = q - 2
+      const int p = (int)q - 2;
+      if (p >= 1 && p <= K + 1) f &= ~clr[(p - 1) * clr_stride];
       const int jj = (int)m - 1 - p;
       if (jj >= 1 && jj <= K + 1) f &= ~clr[(K + jj) * clr_stride];
     }
@@ -435,15 +359,18 @@ __host__ __device__ __forceinline__ void sliced_group(const SlicedArgs &a, uint6
     constexpr int NFULL = M > 0 ? M / L : 0, TAIL = M > 0 ? M % L : 0;
 #pragma unroll 1
     for (int it = 0; it < NFULL; ++it) {
+      cm = corr_bits(q0);
 #pragma unroll
       for (int j = 0; j < L; ++j) step(q0 + (uint32_t)j, j);
       q0 += L;
     }
+    cm = corr_bits(q0);
 #pragma unroll
     for (int j = 0; j < TAIL; ++j) step(q0 + (uint32_t)j, j);
   } else {
     bool more = true;
     while (more) {
+      cm = corr_bits(q0);
 #pragma unroll
       for (int j = 0; j < L; ++j) {
         if (q0 + (uint32_t)j >= m) {
