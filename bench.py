@@ -87,6 +87,22 @@ def ops_per_pair(m: int, e: int) -> int:
     return W * (9 + 22 * ek + 4)
 
 
+def sliced_ops_per_pair(m: int, e: int) -> float:
+    """Integer ops of the bit-sliced formulation (32 pairs per word): per base
+    position, 4 per mask (2 for the difference, 1 AND of the dilation into
+    the running vector, 1 OR carried for the next dilation) for the 2K+1
+    masks, 2 for the erosion and 4 for the count, shared by 32 pairs."""
+    K = min(e, max(m - 1, 0))
+    return m * (8 * K + 10) / 32
+
+
+def sliced_bytes_per_pair(m: int) -> float:
+    """Bytes a sliced filter launch moves per pair: the read and window planes
+    (2 bits per base each, m/2), the status words (8 per 32 pairs) and the
+    accept byte + 16-bit count."""
+    return m / 2 + 8 / 32 + 3
+
+
 def bytes_per_pair(m: int, c: float, per_pair_e: bool) -> float:
     """Algorithmic bytes: offset 4, read id 4/c, packed read + N flag
     (m/4 + 1)/c, reference window m/4 (2 bits/base) + its N bits m/8,
@@ -179,27 +195,34 @@ def make_workload(scale: float, rank: int):
     return synth.config2(scale=scale, seed=shard_seed(rank))
 
 
-def kernel_source_hash() -> str:
-    """Hash of the plain filter kernel's sources (kernel body, instantiation
-    units, shared declarations): a recorded traffic figure is only reported
-    while these are unchanged."""
+def kernel_source_hash(kind: str = "per_pair") -> str:
+    """Hash of a filter kernel's sources (kernel body, instantiation units,
+    shared declarations): a recorded traffic figure is only reported while
+    these are unchanged.  kind: "per_pair" (filter.cuh, filter_w*.cu) or
+    "sliced" (sliced.cuh, sliced_kernels.cuh, sliced_m*.cu)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_14978_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name == "filter.cuh" or name == "gk_internal.cuh" or (name.startswith("filter_w") and name.endswith(".cu")):
+        if kind == "sliced":
+            take = name in ("sliced.cuh", "sliced_kernels.cuh", "gk_internal.cuh") or (
+                name.startswith("sliced_m") and name.endswith(".cu"))
+        else:
+            take = name == "filter.cuh" or name == "gk_internal.cuh" or (
+                name.startswith("filter_w") and name.endswith(".cu"))
+        if take:
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, kind: str = "per_pair"):
     """DRAM bytes per filter launch from the committed ncu summary, if it was
     taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "filter_traffic.json")
+    path = os.path.join(ROOT, "profiles", "filter_traffic.json" if kind == "per_pair" else "sliced_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash(kind):
         return None
     return rec.get("per_launch", {}).get(workload)
 
@@ -323,9 +346,16 @@ def run_mine(args):
     edits = torch.empty(w.n_pairs, dtype=torch.int16, device=dev)
     torch.cuda.synchronize()
 
-    def step(ev=None):
+    sliced_ok = all(gk.sliced_supported(m, e) for e in E_SWEEP)
+    sbuf = torch.empty(gk.gk_sliced_bytes(w.n_pairs, m), dtype=torch.uint8, device=dev) if sliced_ok else None
+
+    def encode():
         gk.gk_encode(asc, w.n_reads, w.stride, fixed_len=m, stride_words=sw, packed=packed, nflag=nflag,
                      stream=stream)
+
+    def step_pp(ev=None):
+        """Per-pair kernels: device encode, then one gk_filter per threshold."""
+        encode()
         for i, e in enumerate(E_SWEEP):
             if ev is not None:
                 ev[i][0].record(stream)
@@ -334,89 +364,121 @@ def run_mine(args):
             if ev is not None:
                 ev[i][1].record(stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    def step_sl(ev=None):
+        """Bit-sliced: device encode, the batch sliced once (ev[0]), then one
+        gk_filter_sliced per threshold."""
+        encode()
+        if ev is not None:
+            ev[0][0].record(stream)
+        gk.gk_slice(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, out=sbuf,
+                    stream=stream)
+        if ev is not None:
+            ev[0][1].record(stream)
+        for i, e in enumerate(E_SWEEP):
+            if ev is not None:
+                ev[i + 1][0].record(stream)
+            gk.gk_filter_sliced(sbuf, w.n_pairs, m, e, accept=accept, edits=edits, stream=stream)
+            if ev is not None:
+                ev[i + 1][1].record(stream)
+
+    def timed(fn, steps, n_seg, clocks=None):
+        """W untimed steps, then `steps` steps between two events on the
+        launching stream, a barrier and a synchronize on both sides.  Returns
+        the total ms (slowest rank), each segment's mean ms (events around
+        the launches) and the clock record."""
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                for _ in range(n_seg)] for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks is not None:
+            clocks.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(steps):
+            fn(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop() if clocks is not None else None
+        total = reduce_max(t0.elapsed_time(t1), world, dev)
+        seg = [statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(steps)) for i in range(n_seg)]
+        return total, seg, clk
 
     uuid = None
     try:
         uuid = "GPU-" + str(props.uuid)
     except Exception:
         pass
-    clocks = ClockSampler(uuid)
-    clocks.start()
-    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-            for _ in E_SWEEP] for _ in range(args.steps)]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_start.record(stream)
-    for k in range(args.steps):
-        step(evs[k])
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    filt_ms = [[evs[k][i][0].elapsed_time(evs[k][i][1]) for i in range(len(E_SWEEP))] for k in range(args.steps)]
-
-    elapsed_ms = reduce_max(elapsed_ms, world, dev)
     pairs_per_step = w.n_pairs * len(E_SWEEP)
-    value = whole_job_rate(pairs_per_step, world, args.steps, elapsed_ms)
-
-    # Dominant kernel: the filter.  Algorithmic ops per launch summed over the
-    # sweep, divided by the summed CUDA-event durations of those launches.
-    per_e_ms = [statistics.mean(filt_ms[k][i] for k in range(args.steps)) for i in range(len(E_SWEEP))]
-    ops = sum(w.n_pairs * ops_per_pair(m, e) for e in E_SWEEP)
-    achieved_tops = ops / (sum(per_e_ms) * 1e-3) / 1e12
-    bpp = bytes_per_pair(m, c, False)
-    achieved_gbs = w.n_pairs * bpp * len(E_SWEEP) / (sum(per_e_ms) * 1e-3) / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_basis = f"{SM_COUNT} SMs x {ALU_LANES_PER_SM_CLK:.0f} int lanes/clk x {SM_MAX_MHZ:.0f} MHz"
+
+    def per_pair_roofline(per_e_ms):
+        """Word formulation: algorithmic ops per launch summed over the sweep,
+        over the summed CUDA-event durations of those launches."""
+        ops = sum(w.n_pairs * ops_per_pair(m, e) for e in E_SWEEP)
+        tops = ops / (sum(per_e_ms) * 1e-3) / 1e12
+        bpp = bytes_per_pair(m, c, False)
+        gbs = w.n_pairs * bpp * len(E_SWEEP) / (sum(per_e_ms) * 1e-3) / 1e9
+        return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-e0..10"),
+                "kernel": "filter_kernel<4, 1, 0> (e 0-1) | filter_pair2_kernel<4> (e 2-10)",
+                "ops_basis": "W*(9 + 22e + 4) per pair (word formulation)", "peak_basis": peak_basis,
+                "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                               "bytes_per_pair": bpp}}
+
+    def sliced_roofline(per_e_ms, slice_ms):
+        """Bit-sliced formulation: its algorithmic ops and bytes per launch,
+        summed over the sweep, over the summed launch durations; 'combined'
+        holds the roofline time (each launch at the slower of its ops at the
+        integer peak and its bytes at the HBM peak) against the measured one."""
+        ops = sum(w.n_pairs * sliced_ops_per_pair(m, e) for e in E_SWEEP)
+        bts = w.n_pairs * sliced_bytes_per_pair(m) * len(E_SWEEP)
+        t = sum(per_e_ms)
+        tops = ops / (t * 1e-3) / 1e12
+        gbs = bts / (t * 1e-3) / 1e9
+        roof_ms = 1e3 * sum(max(w.n_pairs * sliced_ops_per_pair(m, e) / (ALU_PEAK_TOPS * 1e12),
+                                w.n_pairs * sliced_bytes_per_pair(m) / (hbm_peak * 1e9)) for e in E_SWEEP)
+        return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-e0..10", kind="sliced"),
+                "kernel": "sliced_filter_kernel<K, 100> (K = e = 0..10)",
+                "ops_basis": "m*(8K + 10)/32 per pair (bit-sliced formulation)", "peak_basis": peak_basis,
+                "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                               "bytes_per_pair": sliced_bytes_per_pair(m)},
+                "combined": {"roofline_ms": roof_ms, "measured_ms": t, "frac": roof_ms / t},
+                "slice_ms": slice_ms}
+
     probe = probe_alu(torch, gk, stream, args.probe_all)
-
-    # The bit-sliced form of the same step: the batch sliced once (32 pairs per
-    # word, position-major), then one gk_filter_sliced per threshold.
-    sliced = None
-    if all(gk.sliced_supported(m, e) for e in E_SWEEP):
-        sbuf = torch.empty(gk.gk_sliced_bytes(w.n_pairs, m), dtype=torch.uint8, device=dev)
-
-        def step_sliced(ev=None):
-            gk.gk_encode(asc, w.n_reads, w.stride, fixed_len=m, stride_words=sw, packed=packed, nflag=nflag,
-                         stream=stream)
-            if ev is not None:
-                ev[0][0].record(stream)
-            gk.gk_slice(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, out=sbuf,
-                        stream=stream)
-            if ev is not None:
-                ev[0][1].record(stream)
-            for i, e in enumerate(E_SWEEP):
-                if ev is not None:
-                    ev[i + 1][0].record(stream)
-                gk.gk_filter_sliced(sbuf, w.n_pairs, m, e, accept=accept, edits=edits, stream=stream)
-                if ev is not None:
-                    ev[i + 1][1].record(stream)
-
-        for _ in range(args.warmup):
-            step_sliced()
-        sev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-                for _ in range(len(E_SWEEP) + 1)] for _ in range(args.steps)]
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        s0.record(stream)
-        for k in range(args.steps):
-            step_sliced(sev[k])
-        s1.record(stream)
-        torch.cuda.synchronize()
-        sms = s0.elapsed_time(s1) / args.steps
-        seg = [statistics.mean(sev[k][i][0].elapsed_time(sev[k][i][1]) for k in range(args.steps))
-               for i in range(len(E_SWEEP) + 1)]
-        sliced = {"gpairs_s": pairs_per_step / (sms * 1e-3) / 1e9, "ms_per_step": sms, "slice_ms": seg[0],
-                  "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, seg[1:])}}
-        del sbuf
+    clocks = ClockSampler(uuid)
+    if sliced_ok:
+        total_ms, seg, clk = timed(step_sl, args.steps, len(E_SWEEP) + 1, clocks)
+        per_e_ms = seg[1:]
+        roofline = sliced_roofline(per_e_ms, seg[0])
+        step_desc = "device encode + slice once + 11 sliced filter launches"
+        launches_per_step = 2 + len(E_SWEEP)
+        pp_steps = max(3, min(args.steps, 20))
+        pp_total, pp_seg, _ = timed(step_pp, pp_steps, len(E_SWEEP))
+        per_pair = {"gpairs_s": whole_job_rate(pairs_per_step, world, pp_steps, pp_total),
+                    "ms_per_step": pp_total / pp_steps, "steps": pp_steps,
+                    "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, pp_seg)},
+                    "roofline": per_pair_roofline(pp_seg)}
+    else:
+        total_ms, seg, clk = timed(step_pp, args.steps, len(E_SWEEP), clocks)
+        per_e_ms = seg
+        roofline = per_pair_roofline(per_e_ms)
+        step_desc = "device encode + 11 filter launches"
+        launches_per_step = 1 + len(E_SWEEP)
+        per_pair = None
+    elapsed_ms = total_ms
+    value = whole_job_rate(pairs_per_step, world, args.steps, elapsed_ms)
+    roofline["probe_measured_tops"] = {k: v / 1e12 for k, v in probe.items()}
 
     # the paper's device-encoded mode at one threshold (Table 2's e = 2 and 5):
     # ASCII reads encoded inside the filter kernel (gk_filter_ascii) against
@@ -452,7 +514,6 @@ def run_mine(args):
 
     if rank != 0:
         return
-    traffic = recorded_traffic("c2-100bp-e0..10")
     line = {
         "metric": "filtered pairs/s (x10^9), 100 bp, e sweep 0..10",
         "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -460,24 +521,18 @@ def run_mine(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "config 2: 100 bp, 5M reads x 4 candidates, 100 Mbp genome, e=0..10",
                    "pairs": w.n_pairs, "pairs_per_step": pairs_per_step, "read_len": m,
-                   "e_sweep": [E_SWEEP[0], E_SWEEP[-1]], "step": "device encode + 11 filter launches",
+                   "e_sweep": [E_SWEEP[0], E_SWEEP[-1]], "step": step_desc,
                    "l2": f"inputs {(asc.numel() + 8 * w.n_pairs) / 2**20:.0f} MiB per step > L2 "
                          f"(the 25 MiB packed genome stays L2-resident by design)",
                    "parallelism": f"replicas x{world}"},
         "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, per_e_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                     "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
-                     "kernel": "filter_kernel<4, 1, 0> (e 0-1) | filter_pair2_kernel<4> (e 2-10)",
-                     "peak_basis": f"{SM_COUNT} SMs x {ALU_LANES_PER_SM_CLK:.0f} int lanes/clk x {SM_MAX_MHZ:.0f} MHz",
-                     "probe_measured_tops": {k: v / 1e12 for k, v in probe.items()},
-                     "bytes_side": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
-                                    "frac": achieved_gbs / hbm_peak, "bytes_per_pair": bpp}},
-        "gpu_launches": args.steps * (1 + len(E_SWEEP)),
+        "roofline": roofline,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "per_pair_step": per_pair,
         "device_encoded_one_threshold": device_encoded,
-        "sliced_step": sliced,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

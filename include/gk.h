@@ -375,12 +375,17 @@ int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
  * the encoding and filtering of batch i:
  *   copy in   ASCII reads and pairs (waits until the slot's previous batch
  *             has been filtered)
- *   run       gk_encode on the device, then gk_filter once per threshold
- *             (waits for its copy-in and for the slot's previous copy-out)
+ *   run       gk_encode on the device, then the filter at every threshold
+ *             (waits for its copy-in and for the slot's previous copy-out):
+ *             gk_slice once and gk_filter_sliced per threshold when the
+ *             sliced filter covers the pipe (edge OR on, read_len <=
+ *             GK_SLICED_MAX_LEN, every min(e, read_len-1) <=
+ *             GK_SLICED_MAX_SHIFT), else gk_filter per threshold
  *   copy out  accept and edit counts of every threshold
  * Batches hold fixed-length reads (the read length of the pipe).  The pipe
  * owns its device buffers (n_slots * about max_reads * (ascii_stride +
- * 8 * ceil(read_len/32) + 1) + max_pairs * (8 + 3 * n_thresholds) bytes),
+ * 8 * ceil(read_len/32) + 1) + max_pairs * (8 + 3 * n_thresholds) bytes,
+ * plus gk_sliced_bytes(max_pairs, read_len) per slot when it slices),
  * streams and events, all on the device current at creation; every call
  * makes that device current and restores the caller's.  One pipe must not
  * be used from two threads at once.

@@ -28,6 +28,7 @@ struct Slot {
   uint8_t *nflag = nullptr;
   uint8_t *accept = nullptr;
   uint16_t *edits = nullptr;
+  uint8_t *sliced = nullptr;  // the batch in bit-sliced form (when the pipe slices)
   cudaEvent_t in_done = nullptr, run_done = nullptr, out_done = nullptr;
   bool used = false;
 };
@@ -56,6 +57,7 @@ struct gk_pipe_s {
   std::vector<uint8_t> thresholds;
   int count_mode = GK_COUNT_RUNS4;
   uint32_t flags = 0;
+  uint64_t sliced_cap = 0;  // > 0: every batch is sliced once and filtered by gk_filter_sliced
   cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
   Slot slot[kMaxSlots];
   uint64_t next_ticket = 0;
@@ -73,6 +75,7 @@ void release(gk_pipe_s *p) {
     cudaFree(s.nflag);
     cudaFree(s.accept);
     cudaFree(s.edits);
+    cudaFree(s.sliced);
     if (s.in_done) cudaEventDestroy(s.in_done);
     if (s.run_done) cudaEventDestroy(s.run_done);
     if (s.out_done) cudaEventDestroy(s.out_done);
@@ -135,6 +138,13 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
   p->count_mode = d->count_mode;
   p->flags = d->flags;
   const uint64_t n_th = d->n_thresholds;
+  // The bit-sliced filter when it covers the pipe's read length and every
+  // threshold (edge OR on, min(e, m-1) within the compiled shift counts).
+  bool slice = !(d->flags & GK_FLAG_NO_EDGE_FIX) && d->read_len >= 1 && d->read_len <= GK_SLICED_MAX_LEN &&
+               d->max_pairs > 0;
+  for (uint32_t i = 0; slice && i < d->n_thresholds; ++i)
+    slice = (d->thresholds[i] < d->read_len - 1 ? d->thresholds[i] : d->read_len - 1) <= GK_SLICED_MAX_SHIFT;
+  p->sliced_cap = slice ? gk_sliced_bytes(d->max_pairs, d->read_len) : 0;
   bool ok = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking) == cudaSuccess;
@@ -144,6 +154,7 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
          alloc(&s.pair_off, 4 * p->max_pairs) && alloc(&s.packed, 8ull * p->stride_words * p->max_reads) &&
          alloc(&s.nflag, p->max_reads) && alloc(&s.accept, n_th * p->max_pairs) &&
          ((p->flags & GK_FLAG_RESULT_BYTE) || alloc(&s.edits, 2 * n_th * p->max_pairs)) &&
+         (p->sliced_cap == 0 || alloc(&s.sliced, p->sliced_cap)) &&
          cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&s.run_done, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&s.out_done, cudaEventDisableTiming) == cudaSuccess;
@@ -198,11 +209,20 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
                              p->stride_words, s.nflag, 1, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
+  if (p->sliced_cap && n_pairs) {
+    const int rc = gk_slice(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read,
+                            s.pair_off, n_pairs, s.sliced, p->sliced_cap, nullptr, p->s_run);
+    if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
+  }
   for (uint64_t i = 0; i < n_th && n_pairs; ++i) {
-    const int rc = gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read,
-                             s.pair_off, nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags,
-                             s.accept + i * n_pairs, result_byte ? nullptr : s.edits + i * n_pairs, nullptr,
-                             p->s_run);
+    const int rc =
+        p->sliced_cap
+            ? gk_filter_sliced(s.sliced, p->sliced_cap, n_pairs, p->read_len, p->thresholds[i], p->count_mode,
+                               p->flags, s.accept + i * n_pairs, result_byte ? nullptr : s.edits + i * n_pairs,
+                               p->s_run)
+            : gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read, s.pair_off,
+                        nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags, s.accept + i * n_pairs,
+                        result_byte ? nullptr : s.edits + i * n_pairs, nullptr, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
   if (!cuda(cudaEventRecord(s.run_done, p->s_run), "event")) return p->sticky;

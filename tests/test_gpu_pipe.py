@@ -29,9 +29,12 @@ def pinned(a: np.ndarray) -> torch.Tensor:
     return t
 
 
-@pytest.mark.parametrize("n_slots", [2, 3, 4])
-def test_pipe_batches_equal_the_oracle(n_slots):
+@pytest.mark.parametrize("n_slots,ths", [(2, THRESHOLDS), (3, THRESHOLDS), (4, THRESHOLDS), (3, (1, 12))])
+def test_pipe_batches_equal_the_oracle(n_slots, ths):
+    """Thresholds within the sliced filter's shift counts take gk_slice +
+    gk_filter_sliced; a set with e = 12 takes gk_filter."""
     require_gpu()
+    THRESHOLDS = ths
     w = synth.config2(scale=0.001, ref_bases=2_000_000)
     ref = gk.gk_load_reference(w.ref)
     cuts = [0, 700, 700, 1900, 2600, 4100, w.n_reads]  # includes an empty batch
