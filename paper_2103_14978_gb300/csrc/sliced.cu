@@ -217,13 +217,16 @@ cudaError_t launch_slice(const SliceArgs &a, uint32_t *err_count, cudaStream_t s
 // ones.
 cudaError_t launch_sliced_filter(int K, const SlicedArgs &a, cudaStream_t stream) {
   if (K < 0 || K > kSlicedMaxK) return cudaErrorInvalidValue;
-  const bool lo = K <= 5;
+#define GK_SLICED_PICK(M) \
+  (K <= 5 ? launch_sliced_m##M##_k0_5(K, a, stream)  \
+          : (K <= 10 ? launch_sliced_m##M##_k6_10(K, a, stream) : launch_sliced_m##M##_k11_15(K, a, stream)))
   switch (a.m) {
-    case 100: return lo ? launch_sliced_m100_k0_5(K, a, stream) : launch_sliced_m100_k6_10(K, a, stream);
-    case 150: return lo ? launch_sliced_m150_k0_5(K, a, stream) : launch_sliced_m150_k6_10(K, a, stream);
-    case 250: return lo ? launch_sliced_m250_k0_5(K, a, stream) : launch_sliced_m250_k6_10(K, a, stream);
-    default: return lo ? launch_sliced_m0_k0_5(K, a, stream) : launch_sliced_m0_k6_10(K, a, stream);
+    case 100: return GK_SLICED_PICK(100);
+    case 150: return GK_SLICED_PICK(150);
+    case 250: return GK_SLICED_PICK(250);
+    default: return GK_SLICED_PICK(0);
   }
+#undef GK_SLICED_PICK
 }
 
 }  // namespace gk
@@ -290,7 +293,7 @@ int gk_filter_sliced(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs, 
   if (result_byte && fixed_e > 252) return fail(GK_ERANGE, "gk_filter_sliced: GK_FLAG_RESULT_BYTE needs fixed_e <= 252");
   const uint32_t K = fixed_e < m - 1 ? fixed_e : m - 1;
   if (K > (uint32_t)gk::kSlicedMaxK)
-    return fail(GK_ERANGE, "gk_filter_sliced: min(e, m-1) above the compiled shift counts (10)");
+    return fail(GK_ERANGE, "gk_filter_sliced: min(e, m-1) above the compiled shift counts (GK_SLICED_MAX_SHIFT)");
   if (!sliced || !accept_out || (!edits_out && !result_byte)) return fail(GK_EINVAL, "gk_filter_sliced: null buffer");
   if (!aligned_to(sliced, 16)) return fail(GK_EINVAL, "gk_filter_sliced: sliced buffer must be 16-byte aligned");
   if (sliced_cap < gk::sliced_bytes(n_pairs, m)) return fail(GK_EINVAL, "gk_filter_sliced: sliced buffer too small");

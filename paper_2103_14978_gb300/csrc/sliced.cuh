@@ -270,16 +270,17 @@ __host__ __device__ __forceinline__ void sliced_group(const SlicedArgs &a, uint6
   // Positions q0 .. q0+L-1 with an end correction (q in 3..K+3, the low
   // corrections at p = q-2 in 1..K+1, or q in m-K..m-1, the high ones): one
   // bit per position, so the other positions pay one bit test.
-  auto corr_bits = [&](uint32_t q0) -> uint32_t {
-    auto range = [](int lo, int hi) -> uint32_t {
+  static_assert(L <= 64, "one correction bit per position of a ring period");
+  auto corr_bits = [&](uint32_t q0) -> uint64_t {
+    auto range = [](int lo, int hi) -> uint64_t {
       lo = lo < 0 ? 0 : lo;
-      hi = hi > 31 ? 31 : hi;
-      if (hi < lo) return 0u;
-      return (hi == 31 ? 0xffffffffu : ((2u << hi) - 1u)) & ~((1u << lo) - 1u);
+      hi = hi > L - 1 ? L - 1 : hi;
+      if (hi < lo) return 0ull;
+      return (hi == 63 ? ~0ull : ((2ull << hi) - 1ull)) & ~((1ull << lo) - 1ull);
     };
     return range(3 - (int)q0, K + 3 - (int)q0) | range((int)m - K - (int)q0, (int)m - 1 - (int)q0);
   };
-  uint32_t cm = 0;
+  uint64_t cm = 0;
   // One position: q runs, j = q mod L is a constant after unrolling.
   auto step = [&](uint32_t q, int j) {
     // Read position q + K + D into the slot position q - K - 1 leaves, and
@@ -318,7 +319,7 @@ __host__ __device__ __forceinline__ void sliced_group(const SlicedArgs &a, uint6
     uint32_t f = v & accn;
     v = aprev & accn;
     aprev = accn;
-    if ((cm >> j) & 1u) {  // an end correction at p = q - 2
+    if ((cm >> j) & 1ull) {  // an end correction at p = q - 2
       const int p = (int)q - 2;
       if (p >= 1 && p <= K + 1) f &= ~clr[(p - 1) * clr_stride];
       const int jj = (int)m - 1 - p;
@@ -476,7 +477,8 @@ cudaError_t launch_slice(const SliceArgs &a, uint32_t *err_count, cudaStream_t s
 cudaError_t launch_sliced_filter(int K, const SlicedArgs &a, cudaStream_t stream);
 #define GK_SLICED_LAUNCHERS(M)                                                                  \
   cudaError_t launch_sliced_m##M##_k0_5(int K, const SlicedArgs &a, cudaStream_t stream);  \
-  cudaError_t launch_sliced_m##M##_k6_10(int K, const SlicedArgs &a, cudaStream_t stream);
+  cudaError_t launch_sliced_m##M##_k6_10(int K, const SlicedArgs &a, cudaStream_t stream); \
+  cudaError_t launch_sliced_m##M##_k11_15(int K, const SlicedArgs &a, cudaStream_t stream);
 GK_SLICED_LAUNCHERS(0)
 GK_SLICED_LAUNCHERS(100)
 GK_SLICED_LAUNCHERS(150)

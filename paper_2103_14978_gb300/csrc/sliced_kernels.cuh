@@ -9,10 +9,11 @@ namespace gk {
 namespace {
 
 // Resident 128-thread blocks per SM the register budget is set for: the
-// read ring takes 3 words per slot (16 slots up to K = 6, 24 from K = 7).
+// read ring takes 3 words per slot (16 slots up to K = 6, 24 up to K = 10,
+// 32 up to K = 14, 40 at K = 15).
 template <int K>
 struct SlicedMinBlocks {
-  static constexpr int value = K <= 3 ? 4 : 3;
+  static constexpr int value = K <= 3 ? 4 : (K <= 10 ? 3 : 2);
 };
 
 template <int K, int M>

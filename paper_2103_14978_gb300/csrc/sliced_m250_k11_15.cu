@@ -1,0 +1,17 @@
+// Sliced filter kernels, read length 250 bases, shift counts K = 11..15.
+#include "sliced_kernels.cuh"
+
+namespace gk {
+
+cudaError_t launch_sliced_m250_k11_15(int K, const SlicedArgs &a, cudaStream_t stream) {
+  switch (K) {
+    case 11: return launch_sliced_km<11, 250>(a, stream);
+    case 12: return launch_sliced_km<12, 250>(a, stream);
+    case 13: return launch_sliced_km<13, 250>(a, stream);
+    case 14: return launch_sliced_km<14, 250>(a, stream);
+    case 15: return launch_sliced_km<15, 250>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gk

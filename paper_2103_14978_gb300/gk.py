@@ -80,7 +80,7 @@ _SIGS = {
 
 GK_NOALLOC_MAX_PAIRS = 1_000_000
 GK_SLICED_MAX_LEN = 255
-GK_SLICED_MAX_SHIFT = 10
+GK_SLICED_MAX_SHIFT = 15
 GK_GATHER_MAX_BYTES = 65536
 
 

@@ -38,8 +38,8 @@ class SlicedRun:
 
 
 def thresholds(m):
-    """Every threshold the compiled shift counts reach: K = min(e, m-1) <= 10."""
-    es = list(range(0, 11))
+    """Every threshold the compiled shift counts reach: K = min(e, m-1) <= 15."""
+    es = list(range(0, gk.GK_SLICED_MAX_SHIFT + 1))
     if m - 1 <= gk.GK_SLICED_MAX_SHIFT:
         es += [m - 1, m, m + 1, 255]
     return sorted({e for e in es if e <= 255})
@@ -106,6 +106,21 @@ def test_sliced_group_and_block_edges(n):
         assert_same(s.filter(e), oracle_run(w, e), f"n={n} e={e}")
 
 
+@pytest.mark.parametrize("m", [100, 150, 70])
+def test_sliced_pairs_in_any_order(m):
+    """Pairs shuffled (no two candidates of a read side by side, so no read
+    is reused between neighbouring pairs), with N and invalid windows."""
+    w = small_workload(m, 5000, seed=840 + m, n_frac=0.001, read_n_frac=0.001)
+    rng = np.random.default_rng(841)
+    perm = rng.permutation(w.n_pairs)
+    w2 = w.subset(perm)
+    w2.pair_off = w2.pair_off.copy()
+    w2.pair_off[rng.integers(0, w2.n_pairs, 40)] = w.ref.shape[0] - m + rng.integers(1, 50, 40)
+    s = SlicedRun(w2)
+    for e in (0, 1, 5, 10):
+        assert_same(s.filter(e), oracle_run(w2, e), f"shuffled m={m} e={e}")
+
+
 def test_sliced_unaligned_outputs():
     """Result buffers off the 16-byte grid take the scalar stores."""
     w = small_workload(100, 2000, seed=801)
@@ -130,7 +145,7 @@ def test_sliced_config2_structure_scaled():
 def test_sliced_config3_structure_scaled(m):
     w = synth.config3(m, scale=0.002, ref_bases=20_000_000)
     s = SlicedRun(w)
-    for e in (0, 1, 4, 10):
+    for e in (0, 1, 4, 10, 13, 15):
         assert_same(s.filter(e), oracle_run(w, e), f"c3 {m}bp scaled sliced e={e}")
 
 
@@ -154,7 +169,7 @@ def test_sliced_argument_errors_and_empty():
     w = small_workload(100, 64, seed=901, ref_len=10_000)
     s = SlicedRun(w)
     with pytest.raises(gk.GKError) as ex:
-        gk.gk_filter_sliced(s.buf, s.n, 100, 11)  # min(e, m-1) = 11 > 10
+        gk.gk_filter_sliced(s.buf, s.n, 100, 16)  # min(e, m-1) = 16 > 15
     assert ex.value.code == gk.GK_ERANGE
     with pytest.raises(gk.GKError) as ex:
         gk.gk_filter_sliced(s.buf, s.n, 100, 3, flags=gk.GK_FLAG_NO_EDGE_FIX)
