@@ -50,22 +50,25 @@ encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const ui
     for (uint64_t i = threadIdx.x; i < need; i += blockDim.x) tile[i] = src[i];
   }
   __syncthreads();
-  const int total = nseq * (int)stride_words;
   const uint32_t *t32 = reinterpret_cast<const uint32_t *>(tile);
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int s = t / (int)stride_words;
-    const int w = t - s * (int)stride_words;
+  const bool rows4 = (stride & 3) == 0;  // every word starts on 4 bytes: no byte shift
+  auto encode_word = [&](int s, int w) {
     const uint32_t len = (uint32_t)min_u64(lens ? lens[seq0 + s] : fixed_len, stride);
     const int64_t rem = (int64_t)len - 32 * (int64_t)w;
     uint32_t hi = 0, lo = 0, nb = 0;
     if (rem > 0) {
-      // the word's 32 bytes from 9 aligned shared-memory words
+      // the word's 32 bytes from 8 (9 when unaligned) shared-memory words
       const uint64_t o = (uint64_t)s * stride + 32u * (uint64_t)w;
       const uint32_t *src = t32 + (o >> 2);
-      const uint32_t sh = (uint32_t)(o & 3) * 8u;
       uint32_t wb[8];
+      if (rows4) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) wb[j] = __funnelshift_r(src[j], src[j + 1], sh);
+        for (int j = 0; j < 8; ++j) wb[j] = src[j];
+      } else {
+        const uint32_t sh = (uint32_t)(o & 3) * 8u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) wb[j] = __funnelshift_r(src[j], src[j + 1], sh);
+      }
       const uint32_t nv = rem >= 32 ? 32u : (uint32_t)rem;
       encode32_fast(wb, nv, hi, lo, nb);
       if (nb) encode32(wb, nv, hi, lo, nb);  // a non-ACGT byte: exact per-base path
@@ -73,6 +76,16 @@ encode_reads_kernel(const uint8_t *__restrict__ ascii, uint64_t stride, const ui
     uint32_t *out = packed + ((seq0 + s) * (uint64_t)stride_words + w) * 2;
     *reinterpret_cast<uint2 *>(out) = make_uint2(hi, lo);
     if (nb) atomicOr(&undef[s], 1u);
+  };
+  const int sw = (int)stride_words;
+  if ((int)blockDim.x % sw == 0) {  // each thread keeps one word index: no division per word
+    const int w = (int)threadIdx.x % sw, step = (int)blockDim.x / sw;
+    for (int s = (int)threadIdx.x / sw; s < nseq; s += step) encode_word(s, w);
+  } else {
+    for (int t = threadIdx.x; t < nseq * sw; t += blockDim.x) {
+      const int s = t / sw;
+      encode_word(s, t - s * sw);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nseq; i += blockDim.x) nflag[seq0 + i] = (uint8_t)(undef[i] != 0);
