@@ -124,3 +124,31 @@ def test_pipe_rejects_bad_arguments_on_host(libgk):
     assert L.gk_pipe_submit(None, None, 0, None, None, 0, None, None, ctypes.byref(t)) == libgk.GK_EINVAL
     assert L.gk_pipe_wait(None, 0) == libgk.GK_EINVAL
     L.gk_pipe_destroy(None)  # ignored
+
+
+def test_sliced_sizes_and_host_checks(libgk):
+    """gk_sliced_bytes follows the documented layout; gk_slice and
+    gk_filter_sliced reject bad arguments before any device work."""
+    L = libgk.lib()
+    for n, m in ((1, 1), (31, 100), (32, 100), (33, 150), (1024, 250), (20_000_000, 100), (5, 255)):
+        groups = -(-n // 32)
+        pitch = -(-groups // 32) * 32
+        assert L.gk_sliced_bytes(n, m) == (2 * (m + 16) + 1) * pitch * 8, (n, m)
+    assert L.gk_sliced_bytes(0, 100) == 0 and L.gk_sliced_bytes(10, 0) == 0 and L.gk_sliced_bytes(10, 256) == 0
+    buf = ctypes.c_void_p(16)  # never dereferenced: every call below fails its host checks
+    cap = L.gk_sliced_bytes(64, 100)
+    E, R = libgk.GK_EINVAL, libgk.GK_ERANGE
+    assert L.gk_filter_sliced(buf, cap, 64, 0, 3, 0, 0, buf, buf, None) == R  # m = 0
+    assert L.gk_filter_sliced(buf, cap, 64, 256, 3, 0, 0, buf, buf, None) == R  # m > 255
+    assert L.gk_filter_sliced(buf, cap, 64, 100, 16, 0, 0, buf, buf, None) == R  # min(e, m-1) > 15
+    assert L.gk_filter_sliced(buf, cap, 64, 100, 3, 0, libgk.GK_FLAG_NO_EDGE_FIX, buf, buf, None) == E
+    assert L.gk_filter_sliced(buf, cap, 64, 100, 3, 7, 0, buf, buf, None) == E  # count mode
+    assert L.gk_filter_sliced(buf, cap - 8, 64, 100, 3, 0, 0, buf, buf, None) == E  # buffer too small
+    assert L.gk_filter_sliced(None, cap, 64, 100, 3, 0, 0, buf, buf, None) == E
+    assert L.gk_filter_sliced(buf, cap, 64, 100, 253, 0, libgk.GK_FLAG_RESULT_BYTE, buf, None, None) == R
+    assert b"gk_filter_sliced" in L.gk_last_error()
+    assert L.gk_filter_sliced(buf, cap, 0, 100, 3, 0, 0, None, None, None) == libgk.GK_OK  # nothing to do
+    assert L.gk_slice(None, None, 4, 1, None, 100, None, None, 64, buf, cap, None, None) == E  # no reference
+    assert libgk.sliced_supported(100, 15) and not libgk.sliced_supported(100, 16)
+    assert libgk.sliced_supported(5, 255) and not libgk.sliced_supported(17, 255)  # min(e, m-1)
+    assert not libgk.sliced_supported(0, 0) and not libgk.sliced_supported(256, 0)
