@@ -198,7 +198,7 @@ int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride,
 #define GK_SLICED_MAX_SHIFT 15u
 
 /* Bytes of the sliced buffer of n_pairs pairs of read length m:
- * (2(m + 16) + 1) * 8 * (ceil(n_pairs/32) rounded up to 32); 0 when n_pairs is 0 or
+ * (2(m + 24) + 1) * 8 * (ceil(n_pairs/32) rounded up to 32); 0 when n_pairs is 0 or
  * m is outside 1..GK_SLICED_MAX_LEN. */
 uint64_t gk_sliced_bytes(uint64_t n_pairs, uint32_t m);
 

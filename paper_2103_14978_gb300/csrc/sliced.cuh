@@ -43,11 +43,13 @@
 
 namespace gk {
 
-constexpr int kSliceThreads = 128;   // slice: one thread per group
+constexpr int kSliceThreads = 128;   // slice: four lanes per group, 32 groups per block
 constexpr int kSlicedThreads = 128;  // filter: one thread per group
 constexpr int kSlicedMaxK = (int)GK_SLICED_MAX_SHIFT;  // largest shift count with a compiled filter
 constexpr uint32_t kSlicedMaxLen = GK_SLICED_MAX_LEN;
-constexpr uint32_t kSlicedPad = 16;  // rows past m: the ring's prefetch reads up to m - 1 + (L - K - 1)
+// Rows past m in each plane array: the ring's prefetch reads up to row
+// m - 1 + (L - K - 1), at most m + 23 (K = 15: L = 40).
+constexpr uint32_t kSlicedPad = 24;
 
 __host__ __device__ __forceinline__ uint64_t sliced_groups(uint64_t n_pairs) { return (n_pairs + 31) / 32; }
 __host__ __device__ __forceinline__ uint64_t sliced_pitch(uint64_t n_pairs) {
@@ -166,6 +168,7 @@ template <int K>
 struct SlicedRing {
   static constexpr int L = (2 * K + 4 <= 16) ? 16 : ((2 * K + 4 + 7) / 8) * 8;
   static constexpr int D = L - 2 * K - 1;  // prefetch distance, >= 3
+  static_assert(K + D <= (int)kSlicedPad, "the prefetch stays inside the padding rows");
 };
 
 __host__ __device__ __forceinline__ void csa(uint32_t &acc, uint32_t x, uint32_t y, uint32_t &carry) {

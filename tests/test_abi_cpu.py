@@ -133,7 +133,7 @@ def test_sliced_sizes_and_host_checks(libgk):
     for n, m in ((1, 1), (31, 100), (32, 100), (33, 150), (1024, 250), (20_000_000, 100), (5, 255)):
         groups = -(-n // 32)
         pitch = -(-groups // 32) * 32
-        assert L.gk_sliced_bytes(n, m) == (2 * (m + 16) + 1) * pitch * 8, (n, m)
+        assert L.gk_sliced_bytes(n, m) == (2 * (m + 24) + 1) * pitch * 8, (n, m)
     assert L.gk_sliced_bytes(0, 100) == 0 and L.gk_sliced_bytes(10, 0) == 0 and L.gk_sliced_bytes(10, 256) == 0
     buf = ctypes.c_void_p(16)  # never dereferenced: every call below fails its host checks
     cap = L.gk_sliced_bytes(64, 100)
