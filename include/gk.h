@@ -198,8 +198,9 @@ int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride,
 #define GK_SLICED_MAX_SHIFT 15u
 
 /* Bytes of the sliced buffer of n_pairs pairs of read length m:
- * (2(m + 24) + 1) * 8 * (ceil(n_pairs/32) rounded up to 32); 0 when n_pairs is 0 or
- * m is outside 1..GK_SLICED_MAX_LEN. */
+ * (2(m + 24) + 1) * 8 * (ceil(n_pairs/32) rounded up to 32) + 16 (the last 16
+ * bytes: a header recording m and n_pairs); 0 when n_pairs is 0 or m is
+ * outside 1..GK_SLICED_MAX_LEN. */
 uint64_t gk_sliced_bytes(uint64_t n_pairs, uint32_t m);
 
 /*
@@ -223,7 +224,11 @@ int gk_slice(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
 /*
  * gk_filter_sliced -- filter a sliced batch at threshold fixed_e.
  *   sliced, sliced_cap  a buffer filled by gk_slice with the same n_pairs
- *                       and m (not checked beyond its size)
+ *                       and m; the kernel compares both with the header
+ *                       gk_slice wrote, and on a mismatch (a buffer sliced
+ *                       for another batch, or never sliced) writes the
+ *                       invalid result (accept 0, GK_EDITS_INVALID or
+ *                       GK_RESULT_INVALID) for every pair
  *   fixed_e             0..255; min(fixed_e, m-1) <= GK_SLICED_MAX_SHIFT
  *   count_mode          GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT
  *   flags               0 or GK_FLAG_RESULT_BYTE (fixed_e <= 252);
@@ -236,6 +241,36 @@ int gk_filter_sliced(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs,
                      uint32_t m, uint32_t fixed_e, int count_mode,
                      uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
                      void *stream);
+
+/*
+ * gk_filter_sliced_sweep -- filter a sliced batch at every threshold
+ * e = e_lo .. e_hi (the paper's threshold sweeps, Sec. 4), each result the
+ * same as gk_filter_sliced's at that e.  The 2K+1 masks of shift count K are
+ * those of K-1 plus the two shifted by K, so the running AND of every K
+ * comes out of one pass over the batch's positions: each compiled range of
+ * shift counts (0..5 and 6..10) is one launch that reads the planes once;
+ * a shift count outside the ranges, or a range holding one threshold of the
+ * sweep, takes the single-threshold kernel.
+ *   sliced, sliced_cap, n_pairs, m, count_mode   as gk_filter_sliced
+ *   e_lo, e_hi   thresholds, e_lo <= e_hi <= 255, min(e_hi, m-1) <=
+ *                GK_SLICED_MAX_SHIFT
+ *   flags        0 or GK_FLAG_RESULT_BYTE (e_hi <= 252)
+ *   accept_out   device, the results of threshold e at accept_out +
+ *                (e - e_lo) * out_stride (n_pairs bytes each)
+ *   edits_out    device, likewise (uint16 elements); unused (may be NULL)
+ *                with GK_FLAG_RESULT_BYTE
+ *   out_stride   elements between the rows of consecutive thresholds,
+ *                >= n_pairs (a multiple of 16 with 16-byte aligned
+ *                buffers gives vector stores)
+ *   err_count    device uint32 or NULL: incremented by the pairs of every
+ *                launch whose buffer header does not match (m, n_pairs)
+ * Asynchronous on `stream`; GK_EINVAL / GK_ERANGE before any work for bad
+ * arguments.
+ */
+int gk_filter_sliced_sweep(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs,
+                           uint32_t m, uint32_t e_lo, uint32_t e_hi, int count_mode,
+                           uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
+                           uint64_t out_stride, uint32_t *err_count, void *stream);
 
 /* Tiling of the batched filter (chosen by the autotuner). */
 typedef struct {
@@ -349,6 +384,10 @@ int gk_gather(const uint64_t *dst, const uint64_t *src, const uint64_t *bytes,
  *     GK_ERANGE with a message (use gk_filter_batched then).
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
+ *     The address is kept per device together with the ID of the context it
+ *     belongs to: after a cudaDeviceReset (or a released and re-created
+ *     primary context) the next call sees a new context and looks the
+ *     address up again, so make that call before any capture too.
  *   - All calls share the one array and each call overwrites it.  Calls whose
  *     work overlaps on the GPU (e.g. on two streams without ordering) race
  *     and give wrong results: keep them ordered on one stream or serialise
@@ -377,10 +416,11 @@ int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
  *             has been filtered)
  *   run       gk_encode on the device, then the filter at every threshold
  *             (waits for its copy-in and for the slot's previous copy-out):
- *             gk_slice once and gk_filter_sliced per threshold when the
- *             sliced filter covers the pipe (edge OR on, read_len <=
- *             GK_SLICED_MAX_LEN, every min(e, read_len-1) <=
- *             GK_SLICED_MAX_SHIFT), else gk_filter per threshold
+ *             gk_slice once and gk_filter_sliced_sweep per run of
+ *             consecutive thresholds when the sliced filter covers the pipe
+ *             (edge OR on, read_len <= GK_SLICED_MAX_LEN, every
+ *             min(e, read_len-1) <= GK_SLICED_MAX_SHIFT), else gk_filter
+ *             per threshold
  *   copy out  accept and edit counts of every threshold
  * Batches hold fixed-length reads (the read length of the pipe).  The pipe
  * owns its device buffers (n_slots * about max_reads * (ascii_stride +

@@ -25,21 +25,58 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// Per device: the scratch address and the unique ID of the context it was
+// looked up in.  A device reset (cudaDeviceReset) or a released and re-created
+// primary context gives a new context ID, and the address is looked up again.
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device with that device current.
+// Driver calls through the runtime's entry-point table, so the library needs
+// no link against libcuda (the CPU-only build and tests load it without a
+// driver).  Signatures as cuda.h declares them; CUcontext is an opaque pointer.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+// Unique ID of the calling thread's current context, or 0 when none is
+// current or the driver does not offer the query.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_mutex
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    looked_up = true;
+  }
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch on the current device, looked up with that
+// device current on the first call and again whenever the device's context
+// has changed since (ID 0, unknown, always looks up).
 int scratch_address(void **out) {
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return gk::cuda_check(err, "gk_filter_batched_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return gk::fail(GK_ERANGE, "gk_filter_batched_noalloc: device index too large");
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void *p = nullptr;
     err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (err != cudaSuccess) return gk::cuda_check(err, "gk_filter_batched_noalloc: cudaGetSymbolAddress");
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context_id();  // the lookup made the primary context current
   }
   *out = g_scratch_addr[dev];
   return GK_OK;

@@ -214,16 +214,21 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
                             s.pair_off, n_pairs, s.sliced, p->sliced_cap, nullptr, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
-  for (uint64_t i = 0; i < n_th && n_pairs; ++i) {
+  for (uint64_t i = 0; i < n_th && n_pairs;) {
+    // Sliced: every run of consecutive thresholds (e, e+1, ...) is one sweep.
+    uint64_t j = i;
+    if (p->sliced_cap)
+      while (j + 1 < n_th && p->thresholds[j + 1] == p->thresholds[j] + 1) ++j;
     const int rc =
         p->sliced_cap
-            ? gk_filter_sliced(s.sliced, p->sliced_cap, n_pairs, p->read_len, p->thresholds[i], p->count_mode,
-                               p->flags, s.accept + i * n_pairs, result_byte ? nullptr : s.edits + i * n_pairs,
-                               p->s_run)
+            ? gk_filter_sliced_sweep(s.sliced, p->sliced_cap, n_pairs, p->read_len, p->thresholds[i],
+                                     p->thresholds[j], p->count_mode, p->flags, s.accept + i * n_pairs,
+                                     result_byte ? nullptr : s.edits + i * n_pairs, n_pairs, nullptr, p->s_run)
             : gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read, s.pair_off,
                         nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags, s.accept + i * n_pairs,
                         result_byte ? nullptr : s.edits + i * n_pairs, nullptr, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
+    i = j + 1;
   }
   if (!cuda(cudaEventRecord(s.run_done, p->s_run), "event")) return p->sticky;
   // copy out

@@ -113,6 +113,8 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(const SliceArgs a,
     if (u) und |= 1u << j;
   }
   if (inv && err_count) atomicAdd(err_count, popc32(inv));
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    *a.hdr = make_uint4(kSlicedMagic, a.m, (uint32_t)a.n_pairs, (uint32_t)(a.n_pairs >> 32));
   uint32_t gund = und << (part * R), ginv = inv << (part * R);
 #pragma unroll
   for (int d = 1; d < kSliceTpg; d <<= 1) {
@@ -229,12 +231,39 @@ cudaError_t launch_sliced_filter(int K, const SlicedArgs &a, cudaStream_t stream
 #undef GK_SLICED_PICK
 }
 
+cudaError_t launch_sliced_sweep(int klo, int khi, const SlicedArgs &a, cudaStream_t stream) {
+  if (!sliced_sweep_range(klo, khi)) return cudaErrorInvalidValue;
+  switch (a.m) {
+    case 100: return launch_sliced_sweep_m100(klo, a, stream);
+    case 150: return launch_sliced_sweep_m150(klo, a, stream);
+    case 250: return launch_sliced_sweep_m250(klo, a, stream);
+    default: return launch_sliced_sweep_m0(klo, a, stream);
+  }
+}
+
 }  // namespace gk
 
 using gk::fail;
 
 namespace {
 bool aligned_to(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Arguments shared by every filter launch over one sliced buffer.
+gk::SlicedArgs sliced_args(const void *sliced, uint64_t n_pairs, uint32_t m, int count_mode, bool result_byte,
+                           uint32_t *err_count) {
+  gk::SlicedArgs a{};
+  a.pitch = gk::sliced_pitch(n_pairs);
+  a.rs = reinterpret_cast<const uint2 *>(sliced);
+  a.gs = a.rs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
+  a.st = a.gs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
+  a.hdr = reinterpret_cast<const uint4 *>(a.st + a.pitch);
+  a.n_pairs = n_pairs;
+  a.m = m;
+  a.runs4 = count_mode == GK_COUNT_RUNS4 ? 1u : 0u;
+  a.result_byte = result_byte ? 1 : 0;
+  a.err_count = err_count;
+  return a;
+}
 }  // namespace
 
 extern "C" {
@@ -274,6 +303,7 @@ int gk_slice(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64_
   a.rs = reinterpret_cast<uint2 *>(sliced);
   a.gs = a.rs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
   a.st = a.gs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
+  a.hdr = reinterpret_cast<uint4 *>(a.st + a.pitch);
   return gk::cuda_check(gk::launch_slice(a, err_count, (cudaStream_t)stream), "gk_slice: launch");
 }
 
@@ -297,20 +327,75 @@ int gk_filter_sliced(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs, 
   if (!sliced || !accept_out || (!edits_out && !result_byte)) return fail(GK_EINVAL, "gk_filter_sliced: null buffer");
   if (!aligned_to(sliced, 16)) return fail(GK_EINVAL, "gk_filter_sliced: sliced buffer must be 16-byte aligned");
   if (sliced_cap < gk::sliced_bytes(n_pairs, m)) return fail(GK_EINVAL, "gk_filter_sliced: sliced buffer too small");
-  gk::SlicedArgs a{};
-  a.pitch = gk::sliced_pitch(n_pairs);
-  a.rs = reinterpret_cast<const uint2 *>(sliced);
-  a.gs = a.rs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
-  a.st = a.gs + (uint64_t)(m + gk::kSlicedPad) * a.pitch;
-  a.n_pairs = n_pairs;
-  a.m = m;
+  gk::SlicedArgs a = sliced_args(sliced, n_pairs, m, count_mode, result_byte, nullptr);
   a.e = fixed_e;
-  a.runs4 = count_mode == GK_COUNT_RUNS4 ? 1u : 0u;
-  a.result_byte = result_byte ? 1 : 0;
+  a.k_first = a.k_last = K;
+  a.out_stride = 0;
   a.vec_out = aligned_to(accept_out, 16) && (result_byte || aligned_to(edits_out, 16)) ? 1 : 0;
   a.accept = accept_out;
   a.edits = result_byte ? nullptr : edits_out;
   return gk::cuda_check(gk::launch_sliced_filter((int)K, a, (cudaStream_t)stream), "gk_filter_sliced: launch");
+}
+
+int gk_filter_sliced_sweep(const void *sliced, uint64_t sliced_cap, uint64_t n_pairs, uint32_t m, uint32_t e_lo,
+                           uint32_t e_hi, int count_mode, uint32_t flags, uint8_t *accept_out, uint16_t *edits_out,
+                           uint64_t out_stride, uint32_t *err_count, void *stream) {
+  gk::clear_error();
+  if (m == 0 || m > gk::kSlicedMaxLen) return fail(GK_ERANGE, "gk_filter_sliced_sweep: m outside 1..255");
+  if (e_lo > e_hi) return fail(GK_EINVAL, "gk_filter_sliced_sweep: e_lo > e_hi");
+  if (e_hi > 255) return fail(GK_ERANGE, "gk_filter_sliced_sweep: e_hi above 255");
+  if (n_pairs == 0) return GK_OK;
+  if (n_pairs > (1ull << 40)) return fail(GK_ERANGE, "gk_filter_sliced_sweep: too many pairs");
+  const bool result_byte = (flags & GK_FLAG_RESULT_BYTE) != 0;
+  if (flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE))
+    return fail(GK_EINVAL, "gk_filter_sliced_sweep: unknown flags");
+  if (flags & GK_FLAG_NO_EDGE_FIX)
+    return fail(GK_EINVAL, "gk_filter_sliced_sweep: computes the Sec. 3.4 edge OR only (use gk_filter without it)");
+  if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
+    return fail(GK_EINVAL, "gk_filter_sliced_sweep: unknown count_mode");
+  if (result_byte && e_hi > 252)
+    return fail(GK_ERANGE, "gk_filter_sliced_sweep: GK_FLAG_RESULT_BYTE needs e_hi <= 252");
+  const uint32_t k_hi = e_hi < m - 1 ? e_hi : m - 1;
+  if (k_hi > (uint32_t)gk::kSlicedMaxK)
+    return fail(GK_ERANGE, "gk_filter_sliced_sweep: min(e_hi, m-1) above the compiled shift counts (GK_SLICED_MAX_SHIFT)");
+  if (!sliced || !accept_out || (!edits_out && !result_byte))
+    return fail(GK_EINVAL, "gk_filter_sliced_sweep: null buffer");
+  if (out_stride < n_pairs) return fail(GK_EINVAL, "gk_filter_sliced_sweep: out_stride < n_pairs");
+  if (!aligned_to(sliced, 16)) return fail(GK_EINVAL, "gk_filter_sliced_sweep: sliced buffer must be 16-byte aligned");
+  if (sliced_cap < gk::sliced_bytes(n_pairs, m))
+    return fail(GK_EINVAL, "gk_filter_sliced_sweep: sliced buffer too small");
+  gk::SlicedArgs a = sliced_args(sliced, n_pairs, m, count_mode, result_byte, err_count);
+  a.out_stride = out_stride;
+  const bool rows16 = (out_stride % 16) == 0;
+  a.vec_out = rows16 && aligned_to(accept_out, 16) && (result_byte || aligned_to(edits_out, 16)) ? 1 : 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  // Thresholds e <= m-1 have the shift count K = e: each compiled range of
+  // shift counts filters its part of [e_lo, e_hi] in one pass (the K below
+  // that part are computed and not written), a K outside every range has
+  // its own launch.  Thresholds above m-1 share K = m-1 and have one launch
+  // each.
+  uint32_t e = e_lo;
+  while (e <= e_hi) {
+    const uint32_t K = e < m - 1 ? e : m - 1;
+    int klo = -1, khi = -1;
+    uint32_t last = e;
+    if (e <= m - 1 && gk::sliced_sweep_cover((int)K, &klo, &khi)) {
+      last = (uint32_t)khi;
+      if (last > e_hi) last = e_hi;
+      if (last > m - 1) last = m - 1;
+    }
+    if (last == e) klo = khi = -1;  // one threshold: the single-count kernel is cheaper
+    a.e = e;
+    a.k_first = K;
+    a.k_last = K + (last - e);
+    a.accept = accept_out + (uint64_t)(e - e_lo) * out_stride;
+    a.edits = result_byte ? nullptr : edits_out + (uint64_t)(e - e_lo) * out_stride;
+    const cudaError_t err = klo >= 0 ? gk::launch_sliced_sweep(klo, khi, a, st) : gk::launch_sliced_filter((int)K, a, st);
+    const int rc = gk::cuda_check(err, "gk_filter_sliced_sweep: launch");
+    if (rc != GK_OK) return rc;
+    e = last + 1;
+  }
+  return GK_OK;
 }
 
 }  // extern "C"

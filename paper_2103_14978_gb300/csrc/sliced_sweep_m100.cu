@@ -1,0 +1,15 @@
+// Sliced sweep kernels, read length 100 bases: the compiled ranges of shift
+// counts, each filtered in one pass.
+#include "sliced_kernels.cuh"
+
+namespace gk {
+
+cudaError_t launch_sliced_sweep_m100(int klo, const SlicedArgs &a, cudaStream_t stream) {
+  switch (klo) {
+    case 0: return launch_sliced_range<0, 5, 100>(a, stream);
+    case 6: return launch_sliced_range<6, 10, 100>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gk

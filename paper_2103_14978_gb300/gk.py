@@ -57,6 +57,9 @@ _SIGS = {
                   _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_filter_sliced": ([_c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_uint32, _c.c_int, _c.c_uint32,
                           _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_sliced_sweep": ([_c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_uint32, _c.c_uint32,
+                                _c.c_int, _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p,
+                                _c.c_void_p], _c.c_int),
     "gk_probe_alu": ([_c.c_int, _c.c_uint32, _c.c_uint32, _c.c_uint32, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_filter_batched_workspace": ([_c.c_uint64], _c.c_uint64),
     "gk_filter_batched": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_void_p,
@@ -339,9 +342,32 @@ def gk_filter_sliced(sliced: torch.Tensor, n_pairs: int, m: int, e: int, count_m
     return accept, (None if result_byte else edits)
 
 
-def accept_of_result_bytes(res: torch.Tensor, e: int) -> torch.Tensor:
-    """Accept bits of GK_FLAG_RESULT_BYTE results at threshold e (<= 252)."""
-    return ((res <= e) | (res == GK_RESULT_UNDEFINED)).to(torch.uint8)
+def gk_filter_sliced_sweep(sliced: torch.Tensor, n_pairs: int, m: int, e_lo: int, e_hi: int,
+                           count_mode: int = GK_COUNT_RUNS4, flags: int = 0, accept: torch.Tensor | None = None,
+                           edits: torch.Tensor | None = None, out_stride: int | None = None,
+                           err_count: torch.Tensor | None = None, stream=None):
+    """Filter a sliced batch at every threshold e_lo..e_hi
+    (gk_filter_sliced_sweep).  Returns (accept, edits) as views of shape
+    (e_hi - e_lo + 1, n_pairs) over the threshold-major buffers (rows
+    out_stride elements apart), or (result bytes, None) with
+    GK_FLAG_RESULT_BYTE; row e - e_lo holds threshold e's results."""
+    dev = sliced.device
+    result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
+    n_e = int(e_hi) - int(e_lo) + 1
+    if out_stride is None:
+        out_stride = -(-n_pairs // 16) * 16
+    if accept is None:
+        accept = torch.empty(max(n_e, 1) * out_stride, dtype=torch.uint8, device=dev)
+    if edits is None and not result_byte:
+        edits = torch.empty(max(n_e, 1) * out_stride, dtype=torch.int16, device=dev)
+    need = (n_e - 1) * out_stride + n_pairs if n_e > 0 else 0
+    _check(lib().gk_filter_sliced_sweep(
+        _dptr(sliced, torch.uint8, "sliced"), sliced.numel(), n_pairs, m, int(e_lo), int(e_hi), count_mode,
+        flags, _dptr(accept, torch.uint8, "accept", need),
+        None if result_byte else _dptr(edits, torch.int16, "edits", need), out_stride,
+        _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    rows = lambda t: t.as_strided((n_e, n_pairs), (out_stride, 1))  # noqa: E731
+    return rows(accept), (None if result_byte else rows(edits))
 
 
 def gk_filter_batched_workspace(n_pairs: int) -> int:

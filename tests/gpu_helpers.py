@@ -51,6 +51,14 @@ def oracle_run(w: synth.Workload, e=None, mode=O.RUNS4, flags=0, idx=None):
     return acc, ed
 
 
+def accept_of_result_bytes(res, e: int) -> np.ndarray:
+    """Accept bits a reader of GK_FLAG_RESULT_BYTE results derives at
+    threshold e (<= 252), as the header documents the format: a count at
+    most e, or the undefined sentinel."""
+    r = res.cpu().numpy() if isinstance(res, torch.Tensor) else np.asarray(res)
+    return ((r <= e) | (r == gk.GK_RESULT_UNDEFINED)).astype(np.uint8)
+
+
 def assert_same(got, want, what=""):
     ga, ge = got
     wa, we = want

@@ -133,7 +133,7 @@ def test_sliced_sizes_and_host_checks(libgk):
     for n, m in ((1, 1), (31, 100), (32, 100), (33, 150), (1024, 250), (20_000_000, 100), (5, 255)):
         groups = -(-n // 32)
         pitch = -(-groups // 32) * 32
-        assert L.gk_sliced_bytes(n, m) == (2 * (m + 24) + 1) * pitch * 8, (n, m)
+        assert L.gk_sliced_bytes(n, m) == (2 * (m + 24) + 1) * pitch * 8 + 16, (n, m)
     assert L.gk_sliced_bytes(0, 100) == 0 and L.gk_sliced_bytes(10, 0) == 0 and L.gk_sliced_bytes(10, 256) == 0
     buf = ctypes.c_void_p(16)  # never dereferenced: every call below fails its host checks
     cap = L.gk_sliced_bytes(64, 100)
@@ -149,6 +149,20 @@ def test_sliced_sizes_and_host_checks(libgk):
     assert b"gk_filter_sliced" in L.gk_last_error()
     assert L.gk_filter_sliced(buf, cap, 0, 100, 3, 0, 0, None, None, None) == libgk.GK_OK  # nothing to do
     assert L.gk_slice(None, None, 4, 1, None, 100, None, None, 64, buf, cap, None, None) == E  # no reference
+    sw = L.gk_filter_sliced_sweep
+    assert sw(buf, cap, 64, 100, 0, 16, 0, 0, buf, buf, 64, None, None) == R  # min(e_hi, m-1) > 15
+    assert sw(buf, cap, 64, 100, 5, 4, 0, 0, buf, buf, 64, None, None) == E  # e_lo > e_hi
+    assert sw(buf, cap, 64, 100, 0, 256, 0, 0, buf, buf, 64, None, None) == R
+    assert sw(buf, cap, 64, 0, 0, 3, 0, 0, buf, buf, 64, None, None) == R  # m = 0
+    assert sw(buf, cap, 64, 100, 0, 10, 0, 0, buf, buf, 63, None, None) == E  # out_stride < n_pairs
+    assert sw(buf, cap - 8, 64, 100, 0, 10, 0, 0, buf, buf, 64, None, None) == E  # buffer too small
+    assert sw(buf, cap, 64, 100, 0, 10, 0, libgk.GK_FLAG_NO_EDGE_FIX, buf, buf, 64, None, None) == E
+    assert sw(buf, cap, 64, 100, 0, 10, 9, 0, buf, buf, 64, None, None) == E  # count mode
+    assert sw(None, cap, 64, 100, 0, 10, 0, 0, buf, buf, 64, None, None) == E
+    assert sw(buf, cap, 64, 100, 0, 10, 0, 0, buf, None, 64, None, None) == E  # edits needed
+    assert sw(buf, cap, 64, 20, 0, 253, 0, libgk.GK_FLAG_RESULT_BYTE, buf, None, 64, None, None) == R
+    assert b"gk_filter_sliced_sweep" in L.gk_last_error()
+    assert sw(buf, cap, 0, 100, 0, 10, 0, 0, None, None, 0, None, None) == libgk.GK_OK  # nothing to do
     assert libgk.sliced_supported(100, 15) and not libgk.sliced_supported(100, 16)
     assert libgk.sliced_supported(5, 255) and not libgk.sliced_supported(17, 255)  # min(e, m-1)
     assert not libgk.sliced_supported(0, 0) and not libgk.sliced_supported(256, 0)

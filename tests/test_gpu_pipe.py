@@ -6,7 +6,7 @@ import pytest
 import torch
 
 from paper_2103_14978_gb300 import gk, synth
-from tests.gpu_helpers import assert_same, oracle_run, require_gpu
+from tests.gpu_helpers import accept_of_result_bytes, assert_same, oracle_run, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -124,7 +124,7 @@ def test_pipe_result_bytes_equal_the_oracle():
             for i, e in enumerate(THRESHOLDS):
                 wa, we = want[e][0][idx], want[e][1][idx]
                 assert np.array_equal(r[i], _result_bytes_of(wa, we)), f"batch {t} e={e}"
-                acc = gk.accept_of_result_bytes(torch.from_numpy(r[i]), e).numpy()
+                acc = accept_of_result_bytes(r[i], e)
                 assert np.array_equal(acc, wa), f"batch {t} e={e}"
     with pytest.raises(gk.GKError):
         gk.Pipe(ref, 10, w.stride, 100, 10, (3, 253), flags=gk.GK_FLAG_RESULT_BYTE)

@@ -1,6 +1,7 @@
 """Bit-exact parity of the bit-sliced batch filter (gk_slice once per batch,
-gk_filter_sliced once per threshold) with the CPU oracle, through the C-ABI:
-every accept bit and edit count identical (integer work, tolerance 0)."""
+gk_filter_sliced once per threshold, gk_filter_sliced_sweep once per range
+of thresholds) with the CPU oracle, through the C-ABI: every accept bit and
+edit count identical (integer work, tolerance 0)."""
 import numpy as np
 import pytest
 import torch
@@ -35,6 +36,17 @@ class SlicedRun:
         if flags & gk.GK_FLAG_RESULT_BYTE:
             return acc.cpu().numpy(), None
         return acc.cpu().numpy(), dd.edits_u16(ed)
+
+    def sweep(self, e_lo, e_hi, mode=gk.GK_COUNT_RUNS4, flags=0, err=None):
+        """Rows e_lo..e_hi of gk_filter_sliced_sweep as {e: (accept, edits)}."""
+        acc, ed = gk.gk_filter_sliced_sweep(self.buf, self.n, self.m, e_lo, e_hi, count_mode=mode, flags=flags,
+                                            err_count=err)
+        torch.cuda.synchronize()
+        out = {}
+        for i, e in enumerate(range(e_lo, e_hi + 1)):
+            a = acc[i].cpu().numpy()
+            out[e] = (a, None) if flags & gk.GK_FLAG_RESULT_BYTE else (a, dd.edits_u16(ed[i]))
+        return out
 
 
 def thresholds(m):
@@ -188,3 +200,93 @@ def test_sliced_argument_errors_and_empty():
     gk.gk_slice(r.ref, r.reads.packed, r.reads.stride_words, r.reads.n_reads, r.reads.nflag, 100, empty, empty)
     acc, ed = gk.gk_filter_sliced(s.buf, 0, 100, 3)
     assert acc.numel() == 0 and ed.numel() == 0
+
+
+SWEEPS = [(0, 10), (0, 5), (6, 10), (2, 4), (3, 9), (5, 6), (7, 15), (0, 15), (10, 12), (4, 4)]
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 8, 11, 31, 33, 64, 100, 127, 150, 250, 255])
+def test_sliced_sweep_matches_oracle(m):
+    """gk_filter_sliced_sweep over ranges that start and end inside, at and
+    across the compiled shift-count ranges (0..5, 6..10) and past them, at
+    lengths where e > m-1 shares K = m-1; N in genome and reads, a ragged
+    last group."""
+    w = small_workload(m, 1500 + 7, seed=1500 + m, n_frac=0.0005, read_n_frac=0.0005)
+    s = SlicedRun(w)
+    want = {}
+    for lo, hi in SWEEPS + ([(0, m + 2)] if m + 2 <= 15 or m - 1 <= 15 else []):
+        got = s.sweep(lo, hi)
+        for e in range(lo, hi + 1):
+            if e not in want:
+                want[e] = oracle_run(w, e)
+            assert_same(got[e], want[e], f"sweep m={m} [{lo},{hi}] e={e}")
+
+
+@pytest.mark.parametrize("m", [100, 150, 70])
+def test_sliced_sweep_popcount_and_result_bytes(m):
+    w = small_workload(m, 3000, seed=1600 + m, n_frac=0.001, read_n_frac=0.001, cands=(8, 64))
+    s = SlicedRun(w)
+    got = s.sweep(0, 10, mode=gk.GK_COUNT_POPCOUNT)
+    for e in range(0, 11):
+        assert_same(got[e], oracle_run(w, e, O.POPCOUNT), f"sweep popcount m={m} e={e}")
+    got = s.sweep(1, 12, flags=gk.GK_FLAG_RESULT_BYTE)
+    for e in range(1, 13):
+        acc, ed = oracle_run(w, e)
+        want = np.where(ed == O.UNDEFINED, gk.GK_RESULT_UNDEFINED,
+                        np.where(ed == O.INVALID, gk.GK_RESULT_INVALID, np.minimum(ed, gk.GK_RESULT_MAX_COUNT)))
+        assert (got[e][0] == want.astype(np.uint8)).all(), f"sweep result bytes m={m} e={e}"
+
+
+def test_sliced_buffer_header_mismatch():
+    """A filter call whose (m, n_pairs) differ from the slice's, or a buffer
+    never sliced: every pair gets the invalid result, and the sweep counts
+    the pairs in its error counter."""
+    w = small_workload(100, 1000, seed=1700, ref_len=20_000)
+    s = SlicedRun(w)
+    assert_same(s.filter(3), oracle_run(w, 3), "header ok")
+    for n, m in ((999, 100), (1000, 99), (1001 - 32, 100)):
+        acc, ed = gk.gk_filter_sliced(s.buf, n, m, 3)
+        torch.cuda.synchronize()
+        assert (acc.cpu().numpy() == 0).all() and (dd.edits_u16(ed) == gk.GK_EDITS_INVALID).all(), (n, m)
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        a2, e2 = gk.gk_filter_sliced_sweep(s.buf, n, m, 0, 10, err_count=err)
+        torch.cuda.synchronize()
+        assert (a2.cpu().numpy() == 0).all() and (dd.edits_u16(e2) == gk.GK_EDITS_INVALID).all()
+        assert int(err.item()) == 2 * n  # two launches (shift counts 0..5 and 6..10), every pair counted
+    fresh = torch.zeros_like(s.buf)
+    acc, _ = gk.gk_filter_sliced(fresh, 1000, 100, 3, flags=gk.GK_FLAG_RESULT_BYTE)
+    torch.cuda.synchronize()
+    assert (acc.cpu().numpy() == gk.GK_RESULT_INVALID).all()
+
+
+def test_sliced_sweep_config2_full_size():
+    """Config 2 at its full size (20M pairs, 100 bp) through the launch form
+    the benchmark times (one sweep over e = 0..10): every pair equal to the
+    per-threshold sliced filter, 20,000 sampled pairs equal to the oracle."""
+    w = synth.config2()
+    s = SlicedRun(w)
+    got = s.sweep(0, 10)
+    rng = np.random.default_rng(2104)
+    idx = np.sort(rng.choice(w.n_pairs, 20_000, replace=False))
+    for e in range(0, 11):
+        single = s.filter(e)
+        assert (single[0] == got[e][0]).all() and (single[1] == got[e][1]).all(), f"c2 sweep vs single e={e}"
+        if e in (0, 3, 6, 10):
+            assert_same((got[e][0][idx], got[e][1][idx]), oracle_run(w, e, idx=idx), f"c2 sweep sampled e={e}")
+
+
+@pytest.mark.parametrize("m", [150, 250])
+def test_sliced_config3_full_size_sampled(m):
+    """Config 3 at its full size (10M pairs, 8-64 candidates per read, N at
+    0.1%), sliced once as the benchmark does: 30,000 sampled pairs against the
+    oracle at e = 0, 8, 15 (single thresholds) and the sweep 0..10."""
+    w = synth.config3(m)
+    s = SlicedRun(w)
+    rng = np.random.default_rng(2105 + m)
+    idx = np.sort(rng.choice(w.n_pairs, 30_000, replace=False))
+    for e in (0, 8, 15):
+        got = s.filter(e)
+        assert_same((got[0][idx], got[1][idx]), oracle_run(w, e, idx=idx), f"c3 {m}bp full sampled e={e}")
+    sw = s.sweep(0, 10)
+    for e in (0, 5, 9, 10):
+        assert_same((sw[e][0][idx], sw[e][1][idx]), oracle_run(w, e, idx=idx), f"c3 {m}bp sweep sampled e={e}")
