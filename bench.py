@@ -62,10 +62,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--es", default="0-10", help="thresholds of the sweep, e.g. 0-10 or 2,10")
     ap.add_argument("--probe-all", action="store_true", help="run every integer probe kind")
-    ap.add_argument("--requests", type=int, default=4000, help="requests per load level (config 5)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: the default line; c3: 150/250 bp with N; c4: batched mixed lengths")
-    ap.add_argument("--tune-seconds", type=float, default=60.0, help="autotuner budget (config 4)")
+    ap.add_argument("--tune-seconds", type=float, default=8.0, help="autotuner budget (config 4)")
+    ap.add_argument("--no-extra", action="store_true", help="config 2 only (no config 3/4/5 keys)")
+    ap.add_argument("--level-seconds", type=float, default=10.0, help="arrival time per serving load level")
     return ap.parse_args()
 
 
@@ -101,6 +102,45 @@ def sliced_bytes_per_pair(m: int) -> float:
     (2 bits per base each, m/2), the status words (8 per 32 pairs) and the
     accept byte + 16-bit count."""
     return m / 2 + 8 / 32 + 3
+
+
+# Shift-count ranges the library's sweep kernels filter in one launch each
+# (gk_filter_sliced_sweep); a threshold outside them is a single launch.
+SWEEP_RANGES = ((0, 5), (6, 10))
+
+
+def sweep_launches(es, m: int):
+    """The launches gk_filter_sliced_sweep makes for the consecutive
+    thresholds es at read length m: [(e_first, e_last, klo, khi)], the
+    kernel of compiled shift counts klo..khi writing e_first..e_last (klo ==
+    khi: a single-threshold kernel)."""
+    out = []
+    e, top = es[0], es[-1]
+    while e <= top:
+        last, klo, khi = e, min(e, m - 1), min(e, m - 1)
+        if e <= m - 1:
+            for lo, hi in SWEEP_RANGES:
+                if lo <= e <= hi and min(hi, top, m - 1) > e:
+                    last, klo, khi = min(hi, top, m - 1), lo, hi
+        out.append((e, last, klo, khi))
+        e = last + 1
+    return out
+
+
+def sweep_ops_per_pair(m: int, klo: int, khi: int) -> float:
+    """Integer ops per pair of one sweep launch over shift counts klo..khi
+    (bit-sliced, 32 pairs per word): per base position 4 per mask for the
+    2*khi+1 masks (the running AND of count K is the one of K-1 with two
+    more masks, so every mask is computed once), and per shift count 2 for
+    the erosion and 4 for the count; klo == khi is sliced_ops_per_pair."""
+    return m * (4 * (2 * khi + 1) + 6 * (khi - klo + 1)) / 32
+
+
+def sweep_bytes_per_pair(m: int, n_written: int, result_byte: bool = False) -> float:
+    """Bytes one sweep launch moves per pair: the planes once (m/2), the
+    status words (8 per 32 pairs), and the results of each threshold it
+    writes (accept + 16-bit count, or one result byte)."""
+    return m / 2 + 8 / 32 + (1 if result_byte else 3) * n_written
 
 
 def bytes_per_pair(m: int, c: float, per_pair_e: bool) -> float:
@@ -365,8 +405,8 @@ def run_mine(args):
                 ev[i][1].record(stream)
 
     def step_sl(ev=None):
-        """Bit-sliced: device encode, the batch sliced once (ev[0]), then one
-        gk_filter_sliced per threshold."""
+        """Bit-sliced, one launch per threshold: device encode, the batch
+        sliced once (ev[0]), then one gk_filter_sliced per threshold."""
         encode()
         if ev is not None:
             ev[0][0].record(stream)
@@ -380,6 +420,36 @@ def run_mine(args):
             gk.gk_filter_sliced(sbuf, w.n_pairs, m, e, accept=accept, edits=edits, stream=stream)
             if ev is not None:
                 ev[i + 1][1].record(stream)
+
+    contiguous = E_SWEEP == list(range(E_SWEEP[0], E_SWEEP[-1] + 1))
+    launches = sweep_launches(E_SWEEP, m) if contiguous else []
+    n_th = len(E_SWEEP)
+    if sliced_ok and contiguous:
+        sw_acc = torch.empty(n_th * w.n_pairs, dtype=torch.uint8, device=dev)
+        sw_ed = torch.empty(n_th * w.n_pairs, dtype=torch.int16, device=dev)
+
+    def step_sw(ev=None):
+        """Bit-sliced sweep: device encode (ev[0]), the batch sliced once
+        (ev[1]), then one gk_filter_sliced_sweep per launch range (ev[2..]):
+        every threshold's results, threshold-major."""
+        if ev is not None:
+            ev[0][0].record(stream)
+        encode()
+        if ev is not None:
+            ev[0][1].record(stream)
+            ev[1][0].record(stream)
+        gk.gk_slice(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, out=sbuf,
+                    stream=stream)
+        if ev is not None:
+            ev[1][1].record(stream)
+        for i, (lo, hi, _, _) in enumerate(launches):
+            if ev is not None:
+                ev[2 + i][0].record(stream)
+            o = (lo - E_SWEEP[0]) * w.n_pairs
+            gk.gk_filter_sliced_sweep(sbuf, w.n_pairs, m, lo, hi, accept=sw_acc[o:], edits=sw_ed[o:],
+                                      out_stride=w.n_pairs, stream=stream)
+            if ev is not None:
+                ev[2 + i][1].record(stream)
 
     def timed(fn, steps, n_seg, clocks=None):
         """W untimed steps, then `steps` steps between two events on the
@@ -448,34 +518,92 @@ def run_mine(args):
                                 w.n_pairs * sliced_bytes_per_pair(m) / (hbm_peak * 1e9)) for e in E_SWEEP)
         return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                 "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-e0..10", kind="sliced"),
-                "kernel": "sliced_filter_kernel<K, 100> (K = e = 0..10)",
+                "kernel": f"sliced_filter_kernel<K, K, {m}> (K = e = {E_SWEEP[0]}..{E_SWEEP[-1]})",
                 "ops_basis": "m*(8K + 10)/32 per pair (bit-sliced formulation)", "peak_basis": peak_basis,
                 "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
                                "bytes_per_pair": sliced_bytes_per_pair(m)},
                 "combined": {"roofline_ms": roof_ms, "measured_ms": t, "frac": roof_ms / t},
                 "slice_ms": slice_ms}
 
+    def sweep_roofline(range_ms, encode_ms, slice_ms):
+        """The sweep launches: their algorithmic ops (sweep_ops_per_pair) and
+        bytes (sweep_bytes_per_pair) over their summed CUDA-event durations;
+        'combined' holds the roofline time (each launch at the slower of its
+        ops at the integer peak and its bytes at the HBM peak) against the
+        measured one; 'survey_basis' the same time against the per-filtration
+        counts of the word formulation (each threshold a separate pass)."""
+        t = sum(range_ms)
+        ops = sum(w.n_pairs * sweep_ops_per_pair(m, klo, khi) for _, _, klo, khi in launches)
+        bts = sum(w.n_pairs * sweep_bytes_per_pair(m, hi - lo + 1) for lo, hi, _, _ in launches)
+        tops = ops / (t * 1e-3) / 1e12
+        gbs = bts / (t * 1e-3) / 1e9
+        roof_ms = 1e3 * sum(max(w.n_pairs * sweep_ops_per_pair(m, klo, khi) / (ALU_PEAK_TOPS * 1e12),
+                                w.n_pairs * sweep_bytes_per_pair(m, hi - lo + 1) / (hbm_peak * 1e9))
+                            for lo, hi, klo, khi in launches)
+        survey_b = w.n_pairs * bytes_per_pair(m, c, False) * n_th
+        survey_ops = sum(w.n_pairs * ops_per_pair(m, e) for e in E_SWEEP)
+        names = [f"sliced_filter_kernel<{klo}, {khi}, {m}>" for _, _, klo, khi in launches]
+        return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-sweep", kind="sliced"),
+                "kernel": " + ".join(names) + " (one launch per shift-count range)",
+                "ops_basis": "m*(4(2*khi+1) + 6(khi-klo+1))/32 per pair and launch (bit-sliced sweep: each mask "
+                             "once per launch, erosion + count per threshold)",
+                "peak_basis": peak_basis,
+                "per_launch_ms": {f"{lo}-{hi}": x for (lo, hi, _, _), x in zip(launches, range_ms)},
+                "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                               "bytes_per_pair": bts / w.n_pairs,
+                               "basis": "planes once per launch (m/2 + 0.25 B) + accept and count per threshold"},
+                "combined": {"roofline_ms": roof_ms, "measured_ms": t, "frac": roof_ms / t},
+                "survey_basis": {
+                    "bytes_per_filtration": bytes_per_pair(m, c, False),
+                    "hbm_frac": survey_b / (t * 1e-3) / 1e9 / hbm_peak,
+                    "word_ops_x_alu_peak": survey_ops / (t * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                    "note": "per-filtration counts (every threshold reading its inputs and building its masks "
+                            "anew); the sweep shares both across the thresholds, so these exceed 1"},
+                "encode_ms": encode_ms, "slice_ms": slice_ms}
+
     probe = probe_alu(torch, gk, stream, args.probe_all)
     clocks = ClockSampler(uuid)
-    if sliced_ok:
-        total_ms, seg, clk = timed(step_sl, args.steps, len(E_SWEEP) + 1, clocks)
+    per_threshold = None
+    per_pair = None
+    if sliced_ok and contiguous:
+        total_ms, seg, clk = timed(step_sw, args.steps, 2 + len(launches), clocks)
+        roofline = sweep_roofline(seg[2:], seg[0], seg[1])
+        per_e_ms = None
+        step_desc = (f"device encode + slice once + {len(launches)} gk_filter_sliced_sweep launches "
+                     f"({', '.join(f'e {lo}..{hi}' for lo, hi, _, _ in launches)}): the masks of threshold e "
+                     f"are shared with every larger threshold of its launch, the planes read once per launch")
+        launches_per_step = 2 + len(launches)
+        side_steps = max(3, min(args.steps, 20))
+        sl_total, sl_seg, _ = timed(step_sl, side_steps, n_th + 1)
+        per_threshold = {"gpairs_s": whole_job_rate(pairs_per_step, world, side_steps, sl_total),
+                         "ms_per_step": sl_total / side_steps, "steps": side_steps,
+                         "step": "device encode + slice once + one gk_filter_sliced per threshold",
+                         "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, sl_seg[1:])},
+                         "roofline": sliced_roofline(sl_seg[1:], sl_seg[0])}
+        per_threshold["roofline"]["survey_basis"] = {
+            "bytes_per_filtration": bytes_per_pair(m, c, False),
+            "hbm_frac": w.n_pairs * bytes_per_pair(m, c, False) * n_th / (sum(sl_seg[1:]) * 1e-3) / 1e9 / hbm_peak}
+    elif sliced_ok:
+        total_ms, seg, clk = timed(step_sl, args.steps, n_th + 1, clocks)
         per_e_ms = seg[1:]
         roofline = sliced_roofline(per_e_ms, seg[0])
-        step_desc = "device encode + slice once + 11 sliced filter launches"
-        launches_per_step = 2 + len(E_SWEEP)
-        pp_steps = max(3, min(args.steps, 20))
-        pp_total, pp_seg, _ = timed(step_pp, pp_steps, len(E_SWEEP))
-        per_pair = {"gpairs_s": whole_job_rate(pairs_per_step, world, pp_steps, pp_total),
-                    "ms_per_step": pp_total / pp_steps, "steps": pp_steps,
-                    "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, pp_seg)},
-                    "roofline": per_pair_roofline(pp_seg)}
+        step_desc = "device encode + slice once + one sliced filter launch per threshold"
+        launches_per_step = 2 + n_th
     else:
-        total_ms, seg, clk = timed(step_pp, args.steps, len(E_SWEEP), clocks)
+        total_ms, seg, clk = timed(step_pp, args.steps, n_th, clocks)
         per_e_ms = seg
         roofline = per_pair_roofline(per_e_ms)
-        step_desc = "device encode + 11 filter launches"
-        launches_per_step = 1 + len(E_SWEEP)
-        per_pair = None
+        step_desc = "device encode + one filter launch per threshold"
+        launches_per_step = 1 + n_th
+    if sliced_ok:
+        pp_steps = max(3, min(args.steps, 20))
+        pp_total, pp_seg, _ = timed(step_pp, pp_steps, n_th)
+        per_pair = {"gpairs_s": whole_job_rate(pairs_per_step, world, pp_steps, pp_total),
+                    "ms_per_step": pp_total / pp_steps, "steps": pp_steps,
+                    "step": "device encode + one gk_filter (per-pair kernels) per threshold",
+                    "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, pp_seg)},
+                    "roofline": per_pair_roofline(pp_seg)}
     elapsed_ms = total_ms
     value = whole_job_rate(pairs_per_step, world, args.steps, elapsed_ms)
     roofline["probe_measured_tops"] = {k: v / 1e12 for k, v in probe.items()}
@@ -512,6 +640,29 @@ def run_mine(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
 
+    in_mib = (asc.numel() + 8 * w.n_pairs) / 2**20
+    extra = {}
+    if world == 1 and not args.no_extra:
+        # The other configurations, each on its own inputs (the 20M-pair
+        # config 2 buffers are released first).
+        del asc, packed, nflag, pairs, accept, edits, sbuf
+        if sliced_ok and contiguous:
+            del sw_acc, sw_ed
+        ref.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        # A configuration that fails records its error in the line instead of
+        # taking the other measurements down with it.
+        for name, fn in (("c3", lambda: measure_c3(args, hbm_peak)), ("c4", lambda: {"c4": measure_c4(args)}),
+                         ("c5", lambda: {"c5": measure_c5(args)})):
+            try:
+                extra.update(fn())
+            except Exception as exc:  # noqa: BLE001
+                extra[name + "_error"] = f"{type(exc).__name__}: {exc}"
+                print(f"bench: {name} failed: {exc!r}", file=sys.stderr, flush=True)
+        extra["extra_configs_wall_s"] = time.perf_counter() - t0
+
     if rank != 0:
         return
     line = {
@@ -522,18 +673,21 @@ def run_mine(args):
         "config": {"workload": "config 2: 100 bp, 5M reads x 4 candidates, 100 Mbp genome, e=0..10",
                    "pairs": w.n_pairs, "pairs_per_step": pairs_per_step, "read_len": m,
                    "e_sweep": [E_SWEEP[0], E_SWEEP[-1]], "step": step_desc,
-                   "l2": f"inputs {(asc.numel() + 8 * w.n_pairs) / 2**20:.0f} MiB per step > L2 "
+                   "l2": f"inputs {in_mib:.0f} MiB per step > L2 "
                          f"(the 25 MiB packed genome stays L2-resident by design)",
                    "parallelism": f"replicas x{world}"},
-        "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, per_e_ms)},
+        "per_e_gpairs_s": (None if per_e_ms is None else
+                           {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in zip(E_SWEEP, per_e_ms)}),
         "roofline": roofline,
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "per_threshold_sliced_step": per_threshold,
         "per_pair_step": per_pair,
         "device_encoded_one_threshold": device_encoded,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -625,116 +779,124 @@ def time_events(torch, fn, steps, stream):
     return s.elapsed_time(e) / steps
 
 
-def run_config3(args):
+def measure_c3(args, hbm_peak: float) -> dict:
     """Config 3: 10M pairs at 150 bp (e 0..15) and 250 bp (e 0..25), 8-64
-    candidates per read, N at 0.1% of genome and read positions."""
+    candidates per read, N at 0.1% of genome and read positions.  Two forms
+    over the same pairs: the per-pair kernels (gk_filter per threshold; the
+    queue skips undefined pairs) and the sliced batch (gk_slice once,
+    gk_filter_sliced_sweep over the thresholds its shift counts cover,
+    gk_filter above); the line's value is the faster, both reported."""
     import torch
 
     from paper_2103_14978_gb300 import build, device_data as dd, gk, synth
 
     build.build()
     stream = torch.cuda.Stream()
+    steps, warm = max(3, min(args.steps, 10)), max(1, min(args.warmup, 3))
     out = {}
     for m, e_hi in ((150, 15), (250, 25)):
         w = synth.config3(m, scale=args.scale)
+        c = w.n_pairs / w.n_reads
+        es = list(range(0, e_hi + 1))
         ref = gk.gk_load_reference(w.ref)
         reads = dd.upload_reads(w.reads, w.read_len, w.stride, stream=stream)
         pairs = dd.upload_pairs(w.pair_read, w.pair_off, None)
-        acc = torch.empty(w.n_pairs, dtype=torch.uint8, device="cuda")
-        ed = torch.empty(w.n_pairs, dtype=torch.int16, device="cuda")
-        per_e = {}
-        ops = 0
-        for e in range(0, e_hi + 1):
-            f = lambda: gk.gk_filter(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag, m,
-                                     pairs.pair_read, pairs.pair_off, e, accept=acc, edits=ed, stream=stream)
-            for _ in range(args.warmup):
+        n = w.n_pairs
+        acc = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ed = torch.empty(n, dtype=torch.int16, device="cuda")
+
+        def timeit(f):
+            for _ in range(warm):
                 f()
-            per_e[e] = time_events(torch, f, args.steps, stream)
+            return time_events(torch, f, steps, stream)
+
+        per_e = {}
+        for e in es:
+            per_e[e] = timeit(lambda e=e: gk.gk_filter(ref, reads.packed, reads.stride_words, reads.n_reads,
+                                                       reads.nflag, m, pairs.pair_read, pairs.pair_off, e,
+                                                       accept=acc, edits=ed, stream=stream))
         torch.cuda.synchronize()
         undefined = int((dd.edits_u16(ed) == gk.GK_EDITS_UNDEFINED).sum())
-        filtered = w.n_pairs - undefined
-        ops = sum(filtered * ops_per_pair(m, e) for e in per_e)
-        total_ms = sum(per_e.values())
-        per_pair = {
-            "value": w.n_pairs * len(per_e) / (total_ms * 1e-3) / 1e9,
-            "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in per_e.items()},
-            "roofline": {"bound": "alu", "achieved": ops / (total_ms * 1e-3) / 1e12, "peak": ALU_PEAK_TOPS,
-                         "unit": "Tops/s", "frac": ops / (total_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
-                         "note": "algorithmic ops of the filtered (non-N) pairs, word formulation"}}
-        # The sweep with the batch sliced once: gk_filter_sliced for the
-        # thresholds its compiled shift counts cover, gk_filter for the rest.
-        sbuf = torch.empty(gk.gk_sliced_bytes(w.n_pairs, m), dtype=torch.uint8, device="cuda")
-        sl = lambda: gk.gk_slice(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag, m,
-                                 pairs.pair_read, pairs.pair_off, out=sbuf, stream=stream)
-        for _ in range(args.warmup):
-            sl()
-        slice_ms = time_events(torch, sl, args.steps, stream)
-        per_e_sl = {}
-        for e in range(0, e_hi + 1):
-            if not gk.sliced_supported(m, e):
-                per_e_sl[e] = per_e[e]
-                continue
-            f = lambda: gk.gk_filter_sliced(sbuf, w.n_pairs, m, e, accept=acc, edits=ed, stream=stream)
-            for _ in range(args.warmup):
-                f()
-            per_e_sl[e] = time_events(torch, f, args.steps, stream)
-        mixed_ms = slice_ms + sum(per_e_sl.values())
-        mixed = {"value": w.n_pairs * len(per_e_sl) / (mixed_ms * 1e-3) / 1e9,
-                 "form": f"slice once + gk_filter_sliced for e <= {gk.GK_SLICED_MAX_SHIFT}, gk_filter above",
-                 "slice_ms": slice_ms,
-                 "per_e_gpairs_s": {str(e): w.n_pairs / (t * 1e-3) / 1e9 for e, t in per_e_sl.items()}}
-        # The sliced kernels filter every pair of a group, the per-pair queue
-        # only the defined ones: with many undefined pairs (250 bp: half)
-        # the per-pair form wins; the line reports the faster of the two.
-        best = mixed if mixed["value"] >= per_pair["value"] else {**per_pair, "form": "gk_filter per threshold"}
-        out[f"{m}bp"] = {"pairs": w.n_pairs, "undefined_pairs": undefined, "e_sweep": [0, e_hi],
-                         "value": best["value"], "form": best["form"],
-                         "per_e_gpairs_s": best["per_e_gpairs_s"], "sliced": mixed, "per_pair": per_pair}
+        filtered = n - undefined
+        pp_ms = sum(per_e.values())
+        pp_ops = sum(filtered * ops_per_pair(m, e) for e in es)
+        per_pair = {"gpairs_s": n * len(es) / (pp_ms * 1e-3) / 1e9, "ms": pp_ms,
+                    "per_e_gpairs_s": {str(e): n / (t * 1e-3) / 1e9 for e, t in per_e.items()},
+                    "alu_frac": pp_ops / (pp_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                    "alu_basis": "W(13 + 22e) per filtered (non-N) pair, word formulation",
+                    "survey_bytes_frac": n * bytes_per_pair(m, c, False) * len(es) / (pp_ms * 1e-3) / 1e9 / hbm_peak}
+        # sliced: slice once, sweep the covered thresholds, per-pair kernels above
+        cover = [e for e in es if gk.sliced_supported(m, e)]
+        rest = [e for e in es if e not in cover]
+        sbuf = torch.empty(gk.gk_sliced_bytes(n, m), dtype=torch.uint8, device="cuda")
+        sacc = torch.empty(len(cover) * n, dtype=torch.uint8, device="cuda")
+        sed = torch.empty(len(cover) * n, dtype=torch.int16, device="cuda")
+        slice_ms = timeit(lambda: gk.gk_slice(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag, m,
+                                              pairs.pair_read, pairs.pair_off, out=sbuf, stream=stream))
+        launches = sweep_launches(cover, m)
+        launch_ms = []
+        for lo, hi, _, _ in launches:
+            o = (lo - cover[0]) * n
+            launch_ms.append(timeit(lambda lo=lo, hi=hi, o=o: gk.gk_filter_sliced_sweep(
+                sbuf, n, m, lo, hi, accept=sacc[o:], edits=sed[o:], out_stride=n, stream=stream)))
+        sl_ms = slice_ms + sum(launch_ms) + sum(per_e[e] for e in rest)
+        sl_ops = sum(n * sweep_ops_per_pair(m, klo, khi) for _, _, klo, khi in launches)
+        sliced = {"gpairs_s": n * len(es) / (sl_ms * 1e-3) / 1e9, "ms": sl_ms, "slice_ms": slice_ms,
+                  "form": f"slice once + gk_filter_sliced_sweep for e {cover[0]}..{cover[-1]}"
+                          + (f" + gk_filter for e {rest[0]}..{rest[-1]}" if rest else ""),
+                  "per_launch_ms": {f"{lo}-{hi}": t for (lo, hi, _, _), t in zip(launches, launch_ms)},
+                  "sweep_alu_frac": sl_ops / (sum(launch_ms) * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                  "alu_basis": "sweep_ops_per_pair over every pair (the sliced kernels filter N pairs too)",
+                  "survey_bytes_frac": n * bytes_per_pair(m, c, False) * len(es) / (sl_ms * 1e-3) / 1e9 / hbm_peak}
+        best = sliced if sliced["gpairs_s"] >= per_pair["gpairs_s"] else per_pair
+        out[f"c3_{m}bp"] = {
+            "value": best["gpairs_s"], "unit": "Gpairs/s", "form": "sliced" if best is sliced else "per-pair",
+            "pairs": n, "e_sweep": [0, e_hi], "candidates_per_read": c, "undefined_frac": undefined / n,
+            "survey_bytes_frac": best["survey_bytes_frac"], "sliced": sliced, "per_pair": per_pair,
+            "per_e_gpairs_s": per_pair["per_e_gpairs_s"]}
         ref.close()
-        del reads, pairs, acc, ed, sbuf
+        del reads, pairs, acc, ed, sbuf, sacc, sed
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "filtered pairs/s (x10^9), 150/250 bp, e sweeps, 0.1% N (config 3)",
-                      "unit": "Gpairs/s", "n_gpus": 1, "dtype": "u32", "data": "synthetic",
-                      "config": {"workload": "config 3", "scale": args.scale}, "results": out}), flush=True)
+    return out
 
 
-def run_config4(args):
+def measure_c4(args) -> dict:
     """Config 4: 50M pairs, lengths U{50..300}, per-pair e = ceil(rate m),
-    one persistent graph-captured launch with an autotuned tiling, against the
-    plain filter launched once per read length over the same pairs."""
+    shuffled: one graph-captured gk_filter_batched (classify, scan, scatter,
+    persistent filter) with the autotuner's tiling, against the plain filter
+    launched once per read length over the same pairs."""
     import torch
 
     from paper_2103_14978_gb300 import batch, build, device_data as dd, gk, synth
 
     build.build()
     stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
     w = synth.config4(scale=args.scale)
+    t_gen = time.perf_counter() - t_gen
     ref = gk.gk_load_reference(w.ref)
     reads = dd.upload_reads(w.reads, w.read_len, w.stride)
     read_len = dd.as_i16(w.read_len).cuda()
     pairs = dd.upload_pairs(w.pair_read, w.pair_off, w.pair_e)
-    # autotune on a seeded sample of the pairs
-    rng = np.random.default_rng(3)
-    samp = np.sort(rng.choice(w.n_pairs, min(w.n_pairs, 4_000_000), replace=False))
-    sp = dd.upload_pairs(w.pair_read[samp], w.pair_off[samp], w.pair_e[samp])
-    logs = []
     sig = batch.signature(w.read_len, w.pair_read, w.pair_e)
-    if args.tune_seconds > 0:
+    results = {}
+    if args.tune_seconds > 0:  # autotune on a seeded sample of the pairs
+        rng = np.random.default_rng(3)
+        samp = np.sort(rng.choice(w.n_pairs, min(w.n_pairs, 4_000_000), replace=False))
+        sp = dd.upload_pairs(w.pair_read[samp], w.pair_off[samp], w.pair_e[samp])
         best, results = batch.autotune(ref, reads.packed, reads.stride_words, reads.n_reads, read_len,
                                        reads.nflag, sp.pair_read, sp.pair_off, sp.pair_e, reps=2,
-                                       budget_s=args.tune_seconds, log=logs.append)
-        batch.save_table(batch.table_key(sig), best, results)
-    else:  # no tuning: the recorded tiling for this GPU and workload, else the default
-        best, results = batch.lookup(sig) or batch.DEFAULT_TILING, {}
-    del sp
+                                       budget_s=args.tune_seconds)
+        del sp
+    else:
+        best = batch.lookup(sig) or batch.DEFAULT_TILING
     bf = batch.BatchedFilter(ref, reads.packed, reads.stride_words, reads.n_reads, read_len, reads.nflag,
                              pairs.pair_read, pairs.pair_off, pairs.pair_e, best)
     bf.capture()
-    for _ in range(args.warmup):
+    steps = max(3, min(args.steps, 10))
+    for _ in range(max(1, args.warmup)):
         bf.replay()
-    steps = args.steps
     batched_ms = time_events(torch, bf.replay, steps, stream)
-    # plain filter: one launch per read length over pairs grouped by length
     m_pair = w.read_len[w.pair_read]
     order = np.argsort(m_pair, kind="stable")
     ms_sorted = m_pair[order]
@@ -751,37 +913,37 @@ def run_config4(args):
                          gp.pair_read[a:b], gp.pair_off[a:b], gp.pair_e[a:b], accept=acc[a:b], edits=ed[a:b],
                          stream=stream)
 
-    for _ in range(args.warmup):
+    for _ in range(max(1, args.warmup)):
         plain()
     plain_ms = time_events(torch, plain, steps, stream)
     torch.cuda.synchronize()
-    same = bool(torch.equal(acc.cpu()[torch.from_numpy(np.argsort(order))], bf.accept.cpu()) and
-                torch.equal(ed.cpu()[torch.from_numpy(np.argsort(order))], bf.edits.cpu()))
+    inv = torch.from_numpy(np.argsort(order))
+    same = bool(torch.equal(acc.cpu()[inv], bf.accept.cpu()) and torch.equal(ed.cpu()[inv], bf.edits.cpu()))
     Wp = (m_pair.astype(np.int64) + 31) // 32
     ek = np.minimum(w.pair_e.astype(np.int64), m_pair.astype(np.int64) - 1)
     ops = float(np.sum(Wp * (13 + 22 * ek)))
-    line = {
-        "metric": "filtered pairs/s (x10^9), mixed 50-300 bp, per-pair e (config 4)",
-        "value": w.n_pairs / (batched_ms * 1e-3) / 1e9, "unit": "Gpairs/s", "n_gpus": 1,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "config 4: 50M pairs, m U{50..300}, 4 candidates, e=ceil(rate m), shuffled",
-                   "pairs": w.n_pairs, "scale": args.scale, "tiling": list(best), "signature": sig},
+    ref.close()
+    return {
+        "value": w.n_pairs / (batched_ms * 1e-3) / 1e9, "unit": "Gpairs/s", "ms": batched_ms, "steps": steps,
+        "pairs": w.n_pairs, "form": "one CUDA-graph replay of gk_filter_batched (classify, scan, scatter, "
+                                    "persistent filter)",
+        "tiling": {"words_per_thread": best[0], "tile_pairs": best[1], "blocks_per_sm": best[2],
+                   "warps_per_block": best[3], "source": "autotuned on a 4M-pair sample" if results else "table"},
+        "autotune_candidates_ms": {",".join(map(str, k)): v for k, v in results.items()},
         "plain_per_length": {"value": w.n_pairs / (plain_ms * 1e-3) / 1e9, "ms": plain_ms,
                              "launches": int(len(starts)), "identical_results": same},
-        "roofline": {"bound": "alu", "achieved": ops / (batched_ms * 1e-3) / 1e12, "peak": ALU_PEAK_TOPS,
-                     "unit": "Tops/s", "frac": ops / (batched_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
-                     "note": "whole graph (planning + persistent kernel)"},
-        "autotune": {"candidates": {",".join(map(str, k)): v for k, v in results.items()}},
-    }
-    print(json.dumps(line), flush=True)
+        "alu_frac": ops / (batched_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+        "alu_basis": "W(13 + 22 min(e, m-1)) per pair, word formulation, over the whole graph",
+        "generation_s": t_gen}
 
 
-def run_config5(args):
-    """Config 5: serving.  Resident 100 Mbp genome; Poisson arrivals of
-    requests of log-uniform 1k-1M pairs, m in {100, 150, 250}, one
-    e = ceil(rate m) per request; offered load 0.5 / 0.8 / 0.95 of the plain
-    filter's measured capacity on the same mix."""
+def measure_c5(args) -> dict:
+    """Config 5: serving.  The 100 Mbp genome stays resident; requests of
+    log-uniform 1k-1M pairs, m in {100, 150, 250}, one e = ceil(rate m) per
+    request, arrive as a Poisson stream.  First the server's own saturated
+    throughput (arrivals far above it), then offered loads of 0.5 / 0.8 /
+    0.95 of that, each with `level_seconds` of arrivals; latency and rates
+    over the requests that arrive after the first second."""
     import torch
 
     from paper_2103_14978_gb300 import build, gk, serve, synth
@@ -791,58 +953,74 @@ def run_config5(args):
     gkref = gk.gk_load_reference(ref)
     lengths, rates = (100, 150, 250), (0.02, 0.05, 0.10)
     pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000)
-    # plain-filter capacity on the mix: every (m, e) pair equally likely
     stream = torch.cuda.current_stream()
-    per_combo = {}
+    per_combo = {}  # the plain filter on the mix, every (m, e) equally likely
     for m in lengths:
         p = pool.by_len[m]
         n = p["pair_read"][1].shape[0]
-        packed = p["packed"][0].cuda()
-        nflag = p["nflag"][0].cuda()
-        pr = p["pair_read"][0].cuda()
-        po = p["pair_off"][0].cuda()
+        packed, nflag = p["packed"][0].cuda(), p["nflag"][0].cuda()
+        pr, po = p["pair_read"][0].cuda(), p["pair_off"][0].cuda()
         acc = torch.empty(n, dtype=torch.uint8, device="cuda")
         ed = torch.empty(n, dtype=torch.int16, device="cuda")
         for rate in rates:
             e = int(np.ceil(round(rate * m, 9)))
-            f = lambda: gk.gk_filter(gkref, packed, pool.sw, p["lens"][1].shape[0], nflag, m, pr, po, e,
+            f = lambda: gk.gk_filter(gkref, packed, pool.sw, p["lens"][1].shape[0], nflag, m, pr, po, e,  # noqa
                                      accept=acc, edits=ed)
             f()
             per_combo[f"{m}bp_e{e}"] = n / (time_events(torch, f, 5, stream) * 1e-3)
-    capacity = 1.0 / np.mean([1.0 / v for v in per_combo.values()])
+    plain = 1.0 / np.mean([1.0 / v for v in per_combo.values()])
     lo, hi = 1_000, 1_000_000
     mean_size = (hi - lo) / np.log(hi / lo)
     cfg = serve.ServeConfig(mem_cap_bytes=8 << 30, max_round_pairs=8_000_000, copy_results=False)
     ex = serve.GpuExecutor(gkref, cfg)
-    levels = {}
-    for load in (0.5, 0.8, 0.95):
-        plan = serve.poisson_plan(args.requests, load * capacity / mean_size, 2103_14978 + 5 + int(load * 100))
+    skip = 1.0
+
+    def level(rate_pairs_s, seconds, seed, stop=False):
+        plan = serve.poisson_plan_for(seconds, rate_pairs_s / mean_size, seed)
         reqs = [pool.request(q["id"], q["m"], q["e"], q["n_pairs"], q["start"], q["arrival"]) for q in plan]
         srv = serve.Server(ex, cfg)
         t0 = time.perf_counter()
-        srv.run(reqs)
-        wall = time.perf_counter() - t0
-        summ = serve.latency_summary(reqs)
-        summ.update({"offered_gpairs_s": load * capacity / 1e9, "rounds": srv.rounds_launched,
-                     "mean_requests_per_round": float(np.mean(srv.coalesced)), "wall_s": wall,
-                     "requests": len(reqs), "max_inflight_rounds": srv.max_inflight_seen})
-        levels[str(load)] = summ
-    # the same 0.8 load with each round's inputs moved by one gk_gather kernel
-    cfg_g = dataclasses.replace(cfg, gather_inputs=True)
-    plan = serve.poisson_plan(args.requests, 0.8 * capacity / mean_size, 2103_14978 + 5 + 80)
-    reqs = [pool.request(q["id"], q["m"], q["e"], q["n_pairs"], q["start"], q["arrival"]) for q in plan]
-    srv = serve.Server(serve.GpuExecutor(gkref, cfg_g), cfg_g)
-    srv.run(reqs)
-    levels["0.8_gather_kernel"] = serve.latency_summary(reqs)
-    line = {"metric": "serving: p50/p99 latency and pairs/s (config 5)", "unit": "Gpairs/s", "n_gpus": 1,
-            "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "config 5: Poisson requests of 1k-1M pairs, m in {100,150,250}, "
-                                   "e = ceil(rate m), rate in {2,5,10}%", "requests_per_level": args.requests,
-                       "ring_read_slots": ex.n_read_slots, "ring_pair_slots": ex.n_pair_slots},
-            "plain_capacity_gpairs_s": capacity / 1e9,
+        srv.run(reqs, stop_at=seconds if stop else None)
+        summ = serve.steady_state_summary(reqs, min(skip, seconds / 2), seconds)
+        summ.update({"rounds": srv.rounds_launched, "mean_requests_per_round": float(np.mean(srv.coalesced)),
+                     "wall_s": time.perf_counter() - t0, "max_inflight_rounds": srv.max_inflight_seen})
+        return summ
+
+    level(0.5 * plain, 1.0, 2103_14978 + 50)  # warm the rings and the pinned pool
+    sat = level(1.5 * plain, max(3.0, args.level_seconds / 3), 2103_14978 + 51, stop=True)
+    capacity = sat["served_gpairs_s"] * 1e9
+    levels = {}
+    for load in (0.5, 0.8, 0.95):
+        levels[str(load)] = level(load * capacity, args.level_seconds, 2103_14978 + 5 + int(load * 100))
+        levels[str(load)]["load"] = load
+    ok = all(abs(v["served_gpairs_s"] / v["offered_gpairs_s"] - 1) < 0.05 for v in levels.values())
+    mono = levels["0.5"]["p99_ms"] <= levels["0.8"]["p99_ms"] <= levels["0.95"]["p99_ms"]
+    gkref.close()
+    return {"unit": "Gpairs/s", "server_saturated_gpairs_s": sat["served_gpairs_s"],
+            "saturation_run": sat, "plain_filter_capacity_gpairs_s": plain / 1e9,
             "plain_per_combo_gpairs_s": {k: v / 1e9 for k, v in per_combo.items()},
-            "levels": levels}
-    print(json.dumps(line), flush=True)
+            "levels": levels, "served_matches_offered": ok, "p99_rises_with_load": mono,
+            "method": f"Poisson arrivals for {args.level_seconds:g} s per level at 0.5/0.8/0.95 of the server's "
+                      f"saturated throughput (measured first: arrivals at 1.5x the plain filter's capacity, "
+                      f"completions counted until the arrivals stop); "
+                      f"latency = arrival -> results on the host, over requests arriving after {skip:g} s",
+            "ring_read_slots": ex.n_read_slots, "ring_pair_slots": ex.n_pair_slots}
+
+
+def run_config(args, which: str):
+    """One of the other configurations as its own JSON line."""
+    import torch  # noqa: F401
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if which == "c3":
+        out = measure_c3(args, float(peaks.get("hbm_gbs", 6800.0)))
+    elif which == "c4":
+        out = {"c4": measure_c4(args)}
+    else:
+        out = {"c5": measure_c5(args)}
+    print(json.dumps({"metric": f"filtered pairs/s (x10^9), {which}", "n_gpus": 1, "dtype": "u32",
+                      "data": "synthetic", **out}), flush=True)
 
 
 def main():
@@ -851,12 +1029,8 @@ def main():
     E_SWEEP = parse_es(args.es)
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == "c3":
-        run_config3(args)
-    elif args.config == "c4":
-        run_config4(args)
-    elif args.config == "c5":
-        run_config5(args)
+    elif args.config in ("c3", "c4", "c5"):
+        run_config(args, args.config)
     else:
         run_mine(args)
 

@@ -205,9 +205,13 @@ class Server:
         r.read_slot, r.pair_slot, r.status, r.t_admit = rs, ps, "admitted", now
         return True
 
-    def run(self, requests: list, clock=time.perf_counter, idle_sleep: float = 20e-6) -> list:
+    def run(self, requests: list, clock=time.perf_counter, idle_sleep: float = 20e-6,
+            stop_at: float | None = None) -> list:
         """Serve `requests` (sorted by arrival) to completion; returns them with
-        status, timings and (if configured) results."""
+        status, timings and (if configured) results.  With `stop_at` (s from
+        the start) nothing new is launched after that time: the rounds in
+        flight complete, and requests not launched by then keep their status
+        ("queued" or "admitted")."""
         t0 = clock()
         self.ex.start(t0)
         pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
@@ -216,6 +220,11 @@ class Server:
         free_slots = collections.deque(range(self.cfg.n_streams))
         while pending or admitted or inflight:
             now = clock() - t0
+            if stop_at is not None and now > stop_at:
+                if not inflight:
+                    break
+                pending.clear()
+                admitted.clear()
             while inflight and self.ex.done(inflight[0].handle):
                 self._complete(inflight.popleft(), clock() - t0, free_slots)
             if inflight and now - inflight[0].t_dispatch > self.cfg.round_timeout_s:
@@ -266,6 +275,30 @@ class Server:
             self.read_ring.release_oldest()
             self.pair_ring.release_oldest()
         free_slots.append(rnd.slot)
+
+
+def steady_state_summary(requests: list, skip_s: float, window_end_s: float) -> dict:
+    """Rates and latency over the window [skip_s, window_end_s) of a run:
+    offered = pairs of the requests arriving in the window per second;
+    served = pairs of the requests completing in the window per second (all
+    of them, whenever they arrived); latency (arrival -> results on the
+    host, and -> results on the device) percentiles over the requests that
+    arrived in the window, every one of which must have completed."""
+    span = window_end_s - skip_s
+    arrived = [r for r in requests if skip_s <= r.arrival < window_end_s]
+    done_in = [r for r in requests if r.status == "done" and skip_s <= r.t_done < window_end_s]
+    fin = [r for r in arrived if r.status == "done"]
+    out = {"window_s": [skip_s, window_end_s], "requests_in_window": len(arrived),
+           "completed_of_window": len(fin),
+           "offered_gpairs_s": sum(r.n_pairs for r in arrived) / span / 1e9,
+           "served_gpairs_s": sum(r.n_pairs for r in done_in) / span / 1e9}
+    if fin:
+        host = np.array([r.t_done - r.arrival for r in fin]) * 1e3
+        dev = np.array([r.t_device_done - r.arrival for r in fin]) * 1e3
+        out.update({"p50_ms": float(np.percentile(host, 50)), "p99_ms": float(np.percentile(host, 99)),
+                    "max_ms": float(host.max()), "device_p50_ms": float(np.percentile(dev, 50)),
+                    "device_p99_ms": float(np.percentile(dev, 99))})
+    return out
 
 
 def latency_summary(requests: list) -> dict:
@@ -505,3 +538,14 @@ def poisson_plan(n_requests: int, rate_per_s: float, seed: int, size_lo=1_000, s
     starts = rng.integers(0, 1 << 30, n_requests)
     return [dict(id=i, arrival=float(arrivals[i]), n_pairs=int(sizes[i]), m=int(ms[i]), e=int(es[i]),
                  start=int(starts[i])) for i in range(n_requests)]
+
+
+def poisson_plan_for(seconds: float, rate_per_s: float, seed: int, **kw):
+    """poisson_plan with arrivals during `seconds` seconds (the requests
+    arriving before then)."""
+    n = int(rate_per_s * seconds * 1.1) + 64
+    while True:
+        plan = poisson_plan(n, rate_per_s, seed, **kw)
+        if plan[-1]["arrival"] >= seconds:
+            return [q for q in plan if q["arrival"] < seconds]
+        n *= 2

@@ -177,3 +177,42 @@ def test_gather_chunks_split_copies_into_bounded_entries():
             i += 1
         assert covered == z
     assert i == cd.shape[0]
+
+
+def test_stop_time_drains_inflight_and_leaves_the_rest(pool):
+    """With stop_at, rounds launched before the stop complete and nothing is
+    launched after it."""
+    reqs = make_requests(pool, 60, 6, spread=0.2)
+    ref, _ = pool
+    ex = FakeExecutor(ref, 100_000, 400_000, delay=0.01)
+    srv = serve.Server(ex, serve.ServeConfig(stride_words=4, max_read_len=128, max_round_pairs=6000))
+    srv.run(reqs, clock=SimClock(ex), idle_sleep=0, stop_at=0.1)
+    done = [r for r in reqs if r.status == "done"]
+    assert done and len(done) < len(reqs)
+    assert all(r.t_dispatch <= 0.1 + 1e-3 for r in done)
+    assert all(r.status in ("queued", "admitted") for r in reqs if r.status != "done")
+
+
+def test_steady_state_summary_counts_the_window():
+    def req(n, arrival, t_done, status="done"):
+        r = serve.Request(0, np.zeros(0, np.uint32), np.zeros(0, np.uint8), np.zeros(0, np.uint16),
+                          np.zeros(n, np.uint32), np.zeros(n, np.uint32), 0, arrival=arrival)
+        r.status, r.t_done, r.t_device_done = status, t_done, t_done - 0.001
+        return r
+
+    reqs = [req(1000, 0.5, 1.2),   # arrived before the window, completed in it: served only
+            req(2000, 1.5, 1.6),   # in the window both ways, 100 ms
+            req(3000, 2.5, 2.8),   # 300 ms
+            req(4000, 2.9, 3.5)]   # arrived in the window, completed after it: offered only
+    s = serve.steady_state_summary(reqs, 1.0, 3.0)
+    assert s["requests_in_window"] == 3 and s["completed_of_window"] == 3
+    assert abs(s["offered_gpairs_s"] - 9000 / 2.0 / 1e9) < 1e-15
+    assert abs(s["served_gpairs_s"] - 6000 / 2.0 / 1e9) < 1e-15
+    assert abs(s["max_ms"] - 600.0) < 1e-6 and 100.0 <= s["p50_ms"] <= 300.0
+
+
+def test_poisson_plan_for_covers_the_duration():
+    plan = serve.poisson_plan_for(2.0, 500.0, 9)
+    arr = np.array([q["arrival"] for q in plan])
+    assert arr.max() < 2.0 and arr.max() > 1.9 and (np.diff(arr) >= 0).all()
+    assert 800 < len(plan) < 1200  # about 500 per second
