@@ -189,6 +189,28 @@ struct SlicedRing {
   static_assert(K + D <= (int)kSlicedPad, "the prefetch stays inside the padding rows");
 };
 
+// Positions per unrolled loop body.  The body indexes the ring with
+// constants, so one ring period (L positions) is the natural unit; with a
+// large period the warps stall on instruction fetch, and a body of 8
+// positions that rotates the ring registers by 8 slots afterwards (3L moves,
+// 9-15 per position) can run faster.  Which is faster was measured on GB300
+// (20M pairs at 100 bp, 10M at 150 and 250 bp), and the rule follows it:
+//   sweep of shift counts 6..10 (L = 24): rotate (0.60 against 0.75 ms at
+//     100 bp, 0.48 / 0.60 at 150, 0.68 / 0.76 at 250);
+//   sweep 0..5 (L = 16) and one shift count up to 10: one period (rotating
+//     lost 0-18%);
+//   one shift count 11..14 (L = 32): rotate at 100 bp (0.46-0.59 against
+//     0.49-0.61 ms), one period at 150 and 250 bp (rotating lost 15-27%);
+//   one shift count 15 (L = 40): rotate (0.60 / 0.96 at 100 bp, 0.45 / 0.52
+//     at 150, 0.74 / 0.93 at 250).
+template <int KLO, int KHI, int M>
+struct SlicedBody {
+  static constexpr int L = SlicedRing<KHI>::L;
+  static constexpr bool rotate = KLO < KHI ? KHI >= 6 : (KHI >= 15 || (KHI >= 11 && M == 100));
+  static constexpr int U = rotate ? 8 : L;
+  static_assert(L % U == 0, "a chunk divides the ring period");
+};
+
 // Bit planes of count / 8 a group needs: the count is at most m (popcount;
 // the windowed run count is at most m/2 + 2).
 __host__ __device__ constexpr int sliced_count_planes(int M) {
@@ -519,13 +541,34 @@ __host__ __device__ __forceinline__ void sliced_sweep_group(const SlicedArgs &a,
   };
   uint32_t q0 = 0;
   if (M > 0) {
-    constexpr int NFULL = M > 0 ? M / L : 0, TAIL = M > 0 ? M % L : 0;
+    // Chunks of U positions (SlicedBody); with U < L the ring is rotated by U
+    // slots after each chunk, so that at every chunk start the slot of read
+    // position r is (r - q0) mod L and the chunk's code indexes it with
+    // constants.  (U is a multiple of 8: the window slots and the count's
+    // position pattern need no rotation.)
+    constexpr int U = SlicedBody<KLO, KHI, M>::U;
+    constexpr int NFULL = M > 0 ? M / U : 0, TAIL = M > 0 ? M % U : 0;
 #pragma unroll 1
     for (int it = 0; it < NFULL; ++it) {
       cm = corr_bits(q0);
 #pragma unroll
-      for (int j = 0; j < L; ++j) step(q0 + (uint32_t)j, j);
-      q0 += L;
+      for (int j = 0; j < U; ++j) step(q0 + (uint32_t)j, j);
+      q0 += U;
+      if (U < L) {
+        uint32_t th[L], tl[L], tx[L];
+#pragma unroll
+        for (int s = 0; s < L; ++s) {
+          th[s] = rh[(s + U) % L];
+          tl[s] = rl[(s + U) % L];
+          tx[s] = rx[(s + U) % L];
+        }
+#pragma unroll
+        for (int s = 0; s < L; ++s) {
+          rh[s] = th[s];
+          rl[s] = tl[s];
+          rx[s] = tx[s];
+        }
+      }
     }
     cm = corr_bits(q0);
 #pragma unroll
