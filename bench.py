@@ -143,6 +143,23 @@ def sweep_bytes_per_pair(m: int, n_written: int, result_byte: bool = False) -> f
     return m / 2 + 8 / 32 + (1 if result_byte else 3) * n_written
 
 
+def pp_sweep_ops_per_pair(m: int, e_lo: int, e_hi: int) -> float:
+    """Integer ops per pair of one per-pair sweep launch (gk_filter_sweep),
+    word formulation: the Hamming mask and the 2K masks of the largest shift
+    count K = min(e_hi, m-1) once (the survey's 9 + 22K per word), and the
+    count (4 per word) for each of the thresholds."""
+    W = -(-m // 32)
+    K = min(e_hi, max(m - 1, 0))
+    return W * (9 + 22 * K + 4 * (e_hi - e_lo + 1))
+
+
+def pp_sweep_bytes_per_pair(m: int, c: float, n_thresholds: int, result_byte: bool = False) -> float:
+    """Algorithmic bytes per pair of one per-pair sweep launch: the pair's
+    inputs once (bytes_per_pair without its results) and the results of each
+    threshold (accept + 16-bit count, or one result byte)."""
+    return bytes_per_pair(m, c, False) - 3 + (1 if result_byte else 3) * n_thresholds
+
+
 def bytes_per_pair(m: int, c: float, per_pair_e: bool) -> float:
     """Algorithmic bytes: offset 4, read id 4/c, packed read + N flag
     (m/4 + 1)/c, reference window m/4 (2 bits/base) + its N bits m/8,
@@ -428,6 +445,26 @@ def run_mine(args):
         sw_acc = torch.empty(n_th * w.n_pairs, dtype=torch.uint8, device=dev)
         sw_ed = torch.empty(n_th * w.n_pairs, dtype=torch.int16, device=dev)
 
+    sweep_ok = contiguous and all(min(e, m - 1) <= gk.GK_SWEEP_MAX_SHIFT for e in E_SWEEP)
+    if sweep_ok:
+        ps_acc = torch.empty(n_th * w.n_pairs, dtype=torch.uint8, device=dev)
+        ps_ed = torch.empty(n_th * w.n_pairs, dtype=torch.int16, device=dev)
+
+    def step_ps(ev=None):
+        """Per-pair sweep: device encode (ev[0]), then one gk_filter_sweep
+        (ev[1]): every threshold's results, threshold-major, each pair's
+        masks built once up to the largest threshold."""
+        if ev is not None:
+            ev[0][0].record(stream)
+        encode()
+        if ev is not None:
+            ev[0][1].record(stream)
+            ev[1][0].record(stream)
+        gk.gk_filter_sweep(ref, packed, sw, w.n_reads, nflag, m, pairs.pair_read, pairs.pair_off, E_SWEEP[0],
+                           E_SWEEP[-1], accept=ps_acc, edits=ps_ed, out_stride=w.n_pairs, stream=stream)
+        if ev is not None:
+            ev[1][1].record(stream)
+
     def step_sw(ev=None):
         """Bit-sliced sweep: device encode (ev[0]), the batch sliced once
         (ev[1]), then one gk_filter_sliced_sweep per launch range (ev[2..]):
@@ -562,19 +599,68 @@ def run_mine(args):
                             "anew); the sweep shares both across the thresholds, so these exceed 1"},
                 "encode_ms": encode_ms, "slice_ms": slice_ms}
 
+    def pp_sweep_roofline(sweep_ms, encode_ms):
+        """The per-pair sweep launch: its algorithmic ops (pp_sweep_ops_per_pair)
+        and bytes (pp_sweep_bytes_per_pair) over its CUDA-event duration;
+        'survey_basis' the same time against the per-filtration counts (each
+        threshold a separate pass over its inputs and masks)."""
+        ops = w.n_pairs * pp_sweep_ops_per_pair(m, E_SWEEP[0], E_SWEEP[-1])
+        bts = w.n_pairs * pp_sweep_bytes_per_pair(m, c, n_th)
+        tops = ops / (sweep_ms * 1e-3) / 1e12
+        gbs = bts / (sweep_ms * 1e-3) / 1e9
+        survey_b = w.n_pairs * bytes_per_pair(m, c, False) * n_th
+        survey_ops = sum(w.n_pairs * ops_per_pair(m, e) for e in E_SWEEP)
+        W = -(-m // 32)
+        kern = f"filter_pair2_kernel<{W}, 3>" if W <= 4 else f"filter_kernel<{W}, 3, false>"
+        return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-sweep", kind="per_pair"),
+                "kernel": kern + " (gk_filter_sweep, one launch for every threshold)",
+                "ops_basis": "W*(9 + 22*K + 4*n_thresholds) per pair, K = min(e_hi, m-1): the word formulation's "
+                             "masks once up to the largest threshold, the count per threshold",
+                "peak_basis": peak_basis, "launch_ms": sweep_ms,
+                "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                               "bytes_per_pair": bts / w.n_pairs,
+                               "basis": "the pair's inputs once (offset, read id, read, window, N bits) + "
+                                        "accept and count per threshold"},
+                "survey_basis": {
+                    "bytes_per_filtration": bytes_per_pair(m, c, False),
+                    "hbm_frac": survey_b / (sweep_ms * 1e-3) / 1e9 / hbm_peak,
+                    "word_ops_x_alu_peak": survey_ops / (sweep_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                    "note": "per-filtration counts (every threshold reading its inputs and building its masks "
+                            "anew); the sweep shares both across the thresholds, so these exceed 1"},
+                "encode_ms": encode_ms}
+
     probe = probe_alu(torch, gk, stream, args.probe_all)
     clocks = ClockSampler(uuid)
     per_threshold = None
     per_pair = None
-    if sliced_ok and contiguous:
-        total_ms, seg, clk = timed(step_sw, args.steps, 2 + len(launches), clocks)
-        roofline = sweep_roofline(seg[2:], seg[0], seg[1])
+    sliced_sweep = None
+    side_steps = max(3, min(args.steps, 20))
+    if sweep_ok:
+        total_ms, seg, clk = timed(step_ps, args.steps, 2, clocks)
+        roofline = pp_sweep_roofline(seg[1], seg[0])
         per_e_ms = None
-        step_desc = (f"device encode + slice once + {len(launches)} gk_filter_sliced_sweep launches "
-                     f"({', '.join(f'e {lo}..{hi}' for lo, hi, _, _ in launches)}): the masks of threshold e "
-                     f"are shared with every larger threshold of its launch, the planes read once per launch")
-        launches_per_step = 2 + len(launches)
-        side_steps = max(3, min(args.steps, 20))
+        step_desc = (f"device encode + one gk_filter_sweep launch over e = {E_SWEEP[0]}..{E_SWEEP[-1]}: each "
+                     f"pair's masks are built once up to the largest threshold and every threshold's count is "
+                     f"taken from the running AND on the way")
+        launches_per_step = 2
+    if sliced_ok and contiguous:
+        if sweep_ok:
+            sw_total, sw_seg, _ = timed(step_sw, side_steps, 2 + len(launches))
+            sliced_sweep = {
+                "gpairs_s": whole_job_rate(pairs_per_step, world, side_steps, sw_total),
+                "ms_per_step": sw_total / side_steps, "steps": side_steps,
+                "step": (f"device encode + slice once + {len(launches)} gk_filter_sliced_sweep launches "
+                         f"({', '.join(f'e {lo}..{hi}' for lo, hi, _, _ in launches)})"),
+                "roofline": sweep_roofline(sw_seg[2:], sw_seg[0], sw_seg[1])}
+        else:
+            total_ms, seg, clk = timed(step_sw, args.steps, 2 + len(launches), clocks)
+            roofline = sweep_roofline(seg[2:], seg[0], seg[1])
+            per_e_ms = None
+            step_desc = (f"device encode + slice once + {len(launches)} gk_filter_sliced_sweep launches "
+                         f"({', '.join(f'e {lo}..{hi}' for lo, hi, _, _ in launches)}): the masks of threshold e "
+                         f"are shared with every larger threshold of its launch, the planes read once per launch")
+            launches_per_step = 2 + len(launches)
         sl_total, sl_seg, _ = timed(step_sl, side_steps, n_th + 1)
         per_threshold = {"gpairs_s": whole_job_rate(pairs_per_step, world, side_steps, sl_total),
                          "ms_per_step": sl_total / side_steps, "steps": side_steps,
@@ -584,19 +670,19 @@ def run_mine(args):
         per_threshold["roofline"]["survey_basis"] = {
             "bytes_per_filtration": bytes_per_pair(m, c, False),
             "hbm_frac": w.n_pairs * bytes_per_pair(m, c, False) * n_th / (sum(sl_seg[1:]) * 1e-3) / 1e9 / hbm_peak}
-    elif sliced_ok:
+    elif sliced_ok and not sweep_ok:
         total_ms, seg, clk = timed(step_sl, args.steps, n_th + 1, clocks)
         per_e_ms = seg[1:]
         roofline = sliced_roofline(per_e_ms, seg[0])
         step_desc = "device encode + slice once + one sliced filter launch per threshold"
         launches_per_step = 2 + n_th
-    else:
+    elif not sweep_ok:
         total_ms, seg, clk = timed(step_pp, args.steps, n_th, clocks)
         per_e_ms = seg
         roofline = per_pair_roofline(per_e_ms)
         step_desc = "device encode + one filter launch per threshold"
         launches_per_step = 1 + n_th
-    if sliced_ok:
+    if sliced_ok or sweep_ok:
         pp_steps = max(3, min(args.steps, 20))
         pp_total, pp_seg, _ = timed(step_pp, pp_steps, n_th)
         per_pair = {"gpairs_s": whole_job_rate(pairs_per_step, world, pp_steps, pp_total),
@@ -648,6 +734,8 @@ def run_mine(args):
         del asc, packed, nflag, pairs, accept, edits, sbuf
         if sliced_ok and contiguous:
             del sw_acc, sw_ed
+        if sweep_ok:
+            del ps_acc, ps_ed
         ref.close()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
@@ -683,6 +771,7 @@ def run_mine(args):
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "sliced_sweep_step": sliced_sweep,
         "per_threshold_sliced_step": per_threshold,
         "per_pair_step": per_pair,
         "device_encoded_one_threshold": device_encoded,
@@ -751,8 +840,9 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
             "windows_ms_per_step": [x / steps for x in windows],
             "timing": f"median of {E2E_WINDOWS} back-to-back windows of {steps} steps, each the slowest rank's "
                       f"wall clock (the host link is shared with the machine's other GPUs)",
-            "path": "pinned host ASCII reads + pairs -> gk_pipe (copy-in, device encode, 11 x gk_filter, "
-                    "copy-out on three streams, 3 steps in flight) -> results in pinned host memory",
+            "path": "pinned host ASCII reads + pairs -> gk_pipe (copy-in, device encode + one gk_filter_sweep "
+                    "over the thresholds, copy-out on three streams, 3 steps in flight) -> results in pinned "
+                    "host memory",
             "results": fmt}
 
 
@@ -781,11 +871,12 @@ def time_events(torch, fn, steps, stream):
 
 def measure_c3(args, hbm_peak: float) -> dict:
     """Config 3: 10M pairs at 150 bp (e 0..15) and 250 bp (e 0..25), 8-64
-    candidates per read, N at 0.1% of genome and read positions.  Two forms
-    over the same pairs: the per-pair kernels (gk_filter per threshold; the
-    queue skips undefined pairs) and the sliced batch (gk_slice once,
-    gk_filter_sliced_sweep over the thresholds its shift counts cover,
-    gk_filter above); the line's value is the faster, both reported."""
+    candidates per read, N at 0.1% of genome and read positions.  Three forms
+    over the same pairs: the per-pair sweep (one gk_filter_sweep over every
+    threshold; the queue skips undefined pairs), the sliced batch (gk_slice
+    once, gk_filter_sliced_sweep over the thresholds its shift counts cover,
+    gk_filter_sweep above) and the per-pair kernels once per threshold
+    (gk_filter); the line's value is the fastest, all reported."""
     import torch
 
     from paper_2103_14978_gb300 import build, device_data as dd, gk, synth
@@ -825,7 +916,21 @@ def measure_c3(args, hbm_peak: float) -> dict:
                     "alu_frac": pp_ops / (pp_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
                     "alu_basis": "W(13 + 22e) per filtered (non-N) pair, word formulation",
                     "survey_bytes_frac": n * bytes_per_pair(m, c, False) * len(es) / (pp_ms * 1e-3) / 1e9 / hbm_peak}
-        # sliced: slice once, sweep the covered thresholds, per-pair kernels above
+        # per-pair sweep: one launch for every threshold
+        psa = torch.empty(len(es) * n, dtype=torch.uint8, device="cuda")
+        pse = torch.empty(len(es) * n, dtype=torch.int16, device="cuda")
+        ps_ms = timeit(lambda: gk.gk_filter_sweep(ref, reads.packed, reads.stride_words, reads.n_reads, reads.nflag,
+                                                  m, pairs.pair_read, pairs.pair_off, es[0], es[-1], accept=psa,
+                                                  edits=pse, out_stride=n, stream=stream))
+        ps_ops = filtered * pp_sweep_ops_per_pair(m, es[0], es[-1])
+        pp_sweep = {"gpairs_s": n * len(es) / (ps_ms * 1e-3) / 1e9, "ms": ps_ms,
+                    "form": f"one gk_filter_sweep over e {es[0]}..{es[-1]}",
+                    "alu_frac": ps_ops / (ps_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                    "alu_basis": "W(9 + 22K + 4 n_thresholds) per filtered (non-N) pair, K = min(e_hi, m-1)",
+                    "bytes_frac": n * pp_sweep_bytes_per_pair(m, c, len(es)) / (ps_ms * 1e-3) / 1e9 / hbm_peak,
+                    "survey_bytes_frac": n * bytes_per_pair(m, c, False) * len(es) / (ps_ms * 1e-3) / 1e9 / hbm_peak}
+        del psa, pse
+        # sliced: slice once, sweep the covered thresholds, the per-pair sweep above
         cover = [e for e in es if gk.sliced_supported(m, e)]
         rest = [e for e in es if e not in cover]
         sbuf = torch.empty(gk.gk_sliced_bytes(n, m), dtype=torch.uint8, device="cuda")
@@ -839,20 +944,29 @@ def measure_c3(args, hbm_peak: float) -> dict:
             o = (lo - cover[0]) * n
             launch_ms.append(timeit(lambda lo=lo, hi=hi, o=o: gk.gk_filter_sliced_sweep(
                 sbuf, n, m, lo, hi, accept=sacc[o:], edits=sed[o:], out_stride=n, stream=stream)))
-        sl_ms = slice_ms + sum(launch_ms) + sum(per_e[e] for e in rest)
+        rest_ms = 0.0
+        if rest:
+            ra = torch.empty(len(rest) * n, dtype=torch.uint8, device="cuda")
+            rd = torch.empty(len(rest) * n, dtype=torch.int16, device="cuda")
+            rest_ms = timeit(lambda: gk.gk_filter_sweep(ref, reads.packed, reads.stride_words, reads.n_reads,
+                                                        reads.nflag, m, pairs.pair_read, pairs.pair_off, rest[0],
+                                                        rest[-1], accept=ra, edits=rd, out_stride=n, stream=stream))
+            del ra, rd
+        sl_ms = slice_ms + sum(launch_ms) + rest_ms
         sl_ops = sum(n * sweep_ops_per_pair(m, klo, khi) for _, _, klo, khi in launches)
         sliced = {"gpairs_s": n * len(es) / (sl_ms * 1e-3) / 1e9, "ms": sl_ms, "slice_ms": slice_ms,
                   "form": f"slice once + gk_filter_sliced_sweep for e {cover[0]}..{cover[-1]}"
-                          + (f" + gk_filter for e {rest[0]}..{rest[-1]}" if rest else ""),
+                          + (f" + gk_filter_sweep for e {rest[0]}..{rest[-1]}" if rest else ""),
                   "per_launch_ms": {f"{lo}-{hi}": t for (lo, hi, _, _), t in zip(launches, launch_ms)},
                   "sweep_alu_frac": sl_ops / (sum(launch_ms) * 1e-3) / 1e12 / ALU_PEAK_TOPS,
                   "alu_basis": "sweep_ops_per_pair over every pair (the sliced kernels filter N pairs too)",
                   "survey_bytes_frac": n * bytes_per_pair(m, c, False) * len(es) / (sl_ms * 1e-3) / 1e9 / hbm_peak}
-        best = sliced if sliced["gpairs_s"] >= per_pair["gpairs_s"] else per_pair
+        forms = {"per_pair_sweep": pp_sweep, "sliced": sliced, "per_pair": per_pair}
+        best = max(forms, key=lambda k: forms[k]["gpairs_s"])
         out[f"c3_{m}bp"] = {
-            "value": best["gpairs_s"], "unit": "Gpairs/s", "form": "sliced" if best is sliced else "per-pair",
+            "value": forms[best]["gpairs_s"], "unit": "Gpairs/s", "form": best,
             "pairs": n, "e_sweep": [0, e_hi], "candidates_per_read": c, "undefined_frac": undefined / n,
-            "survey_bytes_frac": best["survey_bytes_frac"], "sliced": sliced, "per_pair": per_pair,
+            "survey_bytes_frac": forms[best]["survey_bytes_frac"], **forms,
             "per_e_gpairs_s": per_pair["per_e_gpairs_s"]}
         ref.close()
         del reads, pairs, acc, ed, sbuf, sacc, sed

@@ -160,6 +160,34 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
               uint16_t *edits_out, uint32_t *err_count, void *stream);
 
 /*
+ * gk_filter_sweep -- gk_filter at every threshold e = e_lo .. e_hi (the
+ * paper's threshold sweeps, Sec. 4) in one launch, each result equal to
+ * gk_filter's at that e with the edge OR on.  The 2K+1 masks of shift count
+ * K are those of K-1 and the two shifted by K, so each pair's running AND is
+ * built once up to min(e_hi, m-1) and finished (erosion, end corrections,
+ * count) at every threshold: one pass instead of e_hi - e_lo + 1.  Pairs
+ * with a non-ACGT base are skipped once for all thresholds.
+ *
+ * Arguments as gk_filter, except:
+ *   e_lo, e_hi   thresholds, e_lo <= e_hi <= 255 and min(e_hi, m-1) <=
+ *                GK_SWEEP_MAX_SHIFT (the deferred-erosion form's limit)
+ *   flags        0 or GK_FLAG_RESULT_BYTE (e_hi <= 252); GK_FLAG_NO_EDGE_FIX
+ *                is GK_EINVAL
+ *   accept_out   device, the results of threshold e at accept_out +
+ *                (e - e_lo) * out_stride (n_pairs each)
+ *   edits_out    likewise (uint16 elements); unused with GK_FLAG_RESULT_BYTE
+ *   out_stride   elements between consecutive thresholds' rows, >= n_pairs
+ * Asynchronous on `stream`; argument errors before any work.
+ */
+#define GK_SWEEP_MAX_SHIFT 30u
+int gk_filter_sweep(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words,
+                    uint64_t n_reads, const uint8_t *read_nflag, uint32_t m,
+                    const uint32_t *pair_read, const uint32_t *pair_off, uint32_t e_lo,
+                    uint32_t e_hi, uint64_t n_pairs, int count_mode, uint32_t flags,
+                    uint8_t *accept_out, uint16_t *edits_out, uint64_t out_stride,
+                    uint32_t *err_count, void *stream);
+
+/*
  * gk_filter_ascii -- gk_filter on reads given as ASCII rows, encoded inside
  * the filter kernel (the paper's device-encoded mode, Sec. 3.3, without a
  * separate encoding pass or a packed copy of the reads).  The warp encodes
@@ -416,11 +444,12 @@ int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
  *             has been filtered)
  *   run       gk_encode on the device, then the filter at every threshold
  *             (waits for its copy-in and for the slot's previous copy-out):
- *             gk_slice once and gk_filter_sliced_sweep per run of
- *             consecutive thresholds when the sliced filter covers the pipe
- *             (edge OR on, read_len <= GK_SLICED_MAX_LEN, every
- *             min(e, read_len-1) <= GK_SLICED_MAX_SHIFT), else gk_filter
- *             per threshold
+ *             one gk_filter_sweep per run of consecutive thresholds (e,
+ *             e+1, ...) whose shift counts it covers (edge OR on), else
+ *             gk_filter per threshold; with GK_PIPE_SLICED, gk_slice once
+ *             and gk_filter_sliced_sweep per run when the sliced filter
+ *             covers the pipe (edge OR on, read_len <= GK_SLICED_MAX_LEN,
+ *             every min(e, read_len-1) <= GK_SLICED_MAX_SHIFT)
  *   copy out  accept and edit counts of every threshold
  * Batches hold fixed-length reads (the read length of the pipe).  The pipe
  * owns its device buffers (n_slots * about max_reads * (ascii_stride +
@@ -432,6 +461,9 @@ int gk_filter_batched_noalloc(gk_ref_t ref, const uint32_t *reads,
  */
 typedef struct gk_pipe_s *gk_pipe_t;
 
+#define GK_PIPE_SLICED 4u /* pipe flag: run the sliced filter (gk_slice +
+                             gk_filter_sliced_sweep) where it covers the pipe */
+
 typedef struct {
   uint64_t max_reads;          /* reads per batch, at most (>= 1) */
   uint64_t ascii_stride;       /* bytes between read starts in a batch's ASCII, >= read_len */
@@ -441,7 +473,7 @@ typedef struct {
   const uint8_t *thresholds;   /* host, n_thresholds values of e (copied at creation) */
   int count_mode;              /* GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT */
   uint32_t flags;              /* 0, GK_FLAG_NO_EDGE_FIX, GK_FLAG_RESULT_BYTE
-                                  (then every threshold <= 252) */
+                                  (then every threshold <= 252), GK_PIPE_SLICED */
   uint32_t n_slots;            /* batches in flight, 2..4 */
 } gk_pipe_desc_t;
 

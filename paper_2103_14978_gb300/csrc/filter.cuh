@@ -242,19 +242,36 @@ __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const Pai
 // the window and on which window bases are 'A', so their corrections for all
 // k are computed once per pair; so are the two values of the AND one base
 // outside each end that the final erosion reads.
+template <int W, int NP>
+__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t m, uint32_t K, uint32_t tail,
+                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
+                                                const uint32_t (&rh)[W], const uint32_t (&rl)[W],
+                                                const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
+                                                uint32_t (&count)[NP]);
+
 // Deferred-erosion counts of NP pairs that share one read and one shift
 // count K, each against its own window: the read's +k and -k copies (4W
 // funnel shifts per step) are built once for all NP windows.  rh/rl and
 // gh/gl are the read's and the windows' planes, zero past m.
-template <int W, int NP>
+//
+// SWEEP: the counts of every shift count K = Klo .. K (a threshold sweep):
+// the 2k+1 masks of shift count k are those of k-1 and the two shifted by k,
+// so the running AND after step k is the AND of K = k, and the once-per-pair
+// finish (end values, erosion, corrections, count) runs on it at each k from
+// Klo on; emit(k, count) receives each.  Without SWEEP the finish runs once,
+// for K, into count.
+template <int W, int NP, bool SWEEP = false, typename Emit = int>
 __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m, uint32_t K,
                                                 const uint32_t (&rh)[W], const uint32_t (&rl)[W],
                                                 const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
-                                                uint32_t (&count)[NP]) {
+                                                uint32_t (&count)[NP], uint32_t Klo = 0, Emit emit = 0) {
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 
   uint32_t acc[NP][W], d[W], dn[W];
+  auto finish = [&](uint32_t Kf) {
+    deferred_finish<W, NP>(a, m, Kf, tail, lastmask, acc, rh, rl, gh, gl, count);
+  };
   // dilation of a mask: bit i <- d[i-1] | d[i] | d[i+1], zeros outside the words
   auto dil = [&](const uint32_t (&dd)[W], int w) -> uint32_t {
     const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
@@ -267,6 +284,12 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[j][w]) | (rl[w] ^ gl[j][w]);
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[j][w] = dil(d, w);  // shift 0
+  }
+  if constexpr (SWEEP) {
+    if (Klo == 0) {
+      finish(0);
+      emit(0u, count);
+    }
   }
   {
     uint32_t ph[W], pl[W], nh[W], nl[W];
@@ -308,9 +331,26 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
 #pragma unroll
         for (int w = 0; w < W; ++w) acc[j][w] &= dil(d, w) & dil(dn, w);
       }
+      if constexpr (SWEEP) {
+        if (k >= Klo) {
+          finish(k);
+          emit(k, count);
+        }
+      }
     }
   }
+  if constexpr (!SWEEP) finish(K);
+}
 
+// The once-per-pair end of deferred_counts for shift count K: the AND's
+// values one base outside each end, the erosion, the corrections next to the
+// vacated runs and the count (acc is read, not changed).
+template <int W, int NP>
+__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t m, uint32_t K, uint32_t tail,
+                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
+                                                const uint32_t (&rh)[W], const uint32_t (&rl)[W],
+                                                const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
+                                                uint32_t (&count)[NP]) {
   // ---- once per pair: end values of the AND, corrections, final erosion ----
   const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
   const uint32_t r1k = rangeK & ~1u;       // bits 1..K
@@ -443,12 +483,16 @@ __device__ __forceinline__ int pair_status(const FilterArgs &a, const PairData<W
 }
 
 __device__ __forceinline__ void write_trivial(const FilterArgs &a, uint64_t p, int status) {
-  if (a.result_byte) {
-    a.accept[p] = status == 0 ? 0 : (status == 1 ? GK_RESULT_UNDEFINED : GK_RESULT_INVALID);
-    return;
+  const uint32_t rows = a.sweep_hi >= a.fixed_e ? a.sweep_hi - a.fixed_e + 1 : 1;  // every threshold of a sweep
+  for (uint32_t i = 0; i < rows; ++i) {
+    const uint64_t q = p + i * a.out_stride;
+    if (a.result_byte) {
+      a.accept[q] = status == 0 ? 0 : (status == 1 ? GK_RESULT_UNDEFINED : GK_RESULT_INVALID);
+      continue;
+    }
+    a.accept[q] = status != 2;
+    a.edits[q] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
   }
-  a.accept[p] = status != 2;
-  a.edits[p] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
 }
 
 // The result of a filtered pair: accept bit and count, or the result byte.
@@ -461,10 +505,30 @@ __device__ __forceinline__ void write_count(const FilterArgs &a, uint64_t p, uin
   a.edits[p] = (uint16_t)count;
 }
 
+// Threshold sweep of one loaded pair (VARIANT 3): thresholds e = a.fixed_e ..
+// a.sweep_hi have shift counts K = min(e, m-1); the shift loop runs once to
+// the largest and the results of each K go to its rows (every e >= m-1
+// shares K = m-1).
+template <int W>
+__device__ __forceinline__ void sweep_and_write(const FilterArgs &a, uint64_t p, const PairData<W> &x) {
+  uint32_t rh[W], rl[W], gh[1][W], gl[1][W], count[1];
+  pair_planes<W>(x, rh, rl, gh[0], gl[0]);
+  const uint32_t e_lo = a.fixed_e, e_hi = a.sweep_hi, kmax = x.m - 1;
+  const uint32_t Klo = min(e_lo, kmax), Khi = min(e_hi, kmax);
+  deferred_counts<W, 1, true>(a, x.m, Khi, rh, rl, gh, gl, count, Klo, [&](uint32_t K, const uint32_t (&c)[1]) {
+    const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
+    for (uint32_t e = first; e <= last; ++e) write_count(a, p + (uint64_t)(e - e_lo) * a.out_stride, c[0], e);
+  });
+}
+
 template <int W, int VARIANT>
 __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p, const PairData<W> &x) {
-  const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, x) : filter_loaded<W, VARIANT == 1>(a, x);
-  write_count(a, p, count, x.e);
+  if constexpr (VARIANT == 3) {
+    sweep_and_write<W>(a, p, x);
+  } else {
+    const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, x) : filter_loaded<W, VARIANT == 1>(a, x);
+    write_count(a, p, count, x.e);
+  }
 }
 
 // The classify phase of the compacting loop, in two steps so that the loads
@@ -538,7 +602,8 @@ constexpr size_t compact_smem_bytes() {
 }
 
 // VARIANT 0: any thresholds; 1: every shift count of the launch is < 32;
-// 2: edge OR on and one threshold in 2..30, deferred erosion.
+// 2: edge OR on and one threshold in 2..30, deferred erosion; 3: edge OR on,
+// a sweep of thresholds up to 30, deferred erosion (sweep_and_write).
 //
 // COMPACT false: one thread per pair.  COMPACT true (inputs with many
 // undefined pairs): persistent warps take 32 pairs at a time (their ids
@@ -693,12 +758,13 @@ struct MinBlocks2 {
   static constexpr int value = W <= 2 ? 4 : 3;
 };
 
-// Deferred erosion (VARIANT 2), two pairs per thread: pairs 2t and 2t+1.
-// When both are filtered and share their read (the candidates of one read
-// usually sit next to each other), the read's shifted copies serve both
-// windows: a shift step costs about 13W integer operations per pair instead
-// of 15W.  Otherwise each pair is filtered on its own.
-template <int W>
+// Deferred erosion (VARIANT 2, or the sweep, VARIANT 3), two pairs per
+// thread: pairs 2t and 2t+1.  When both are filtered and share their read
+// (the candidates of one read usually sit next to each other), the read's
+// shifted copies serve both windows: a shift step costs about 13W integer
+// operations per pair instead of 15W.  Otherwise each pair is filtered on its
+// own.
+template <int W, int VARIANT>
 __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_pair2_kernel(const FilterArgs a) {
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t p0 = 2 * t, p1 = p0 + 1;
@@ -731,12 +797,25 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
       gh[1][W - 1] &= lastmask;
       gl[1][W - 1] &= lastmask;
     }
-    deferred_counts<W, 2>(a, a.m, min(a.fixed_e, a.m - 1), rh, rl, gh, gl, count);
-    write_count(a, p0, count[0], a.fixed_e);
-    write_count(a, p1, count[1], a.fixed_e);
+    if constexpr (VARIANT == 3) {
+      const uint32_t e_lo = a.fixed_e, e_hi = a.sweep_hi, kmax = a.m - 1;
+      deferred_counts<W, 2, true>(a, a.m, min(e_hi, kmax), rh, rl, gh, gl, count, min(e_lo, kmax),
+                                  [&](uint32_t K, const uint32_t (&c)[2]) {
+                                    const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
+                                    for (uint32_t e = first; e <= last; ++e) {
+                                      const uint64_t o = (uint64_t)(e - e_lo) * a.out_stride;
+                                      write_count(a, p0 + o, c[0], e);
+                                      write_count(a, p1 + o, c[1], e);
+                                    }
+                                  });
+    } else {
+      deferred_counts<W, 2>(a, a.m, min(a.fixed_e, a.m - 1), rh, rl, gh, gl, count);
+      write_count(a, p0, count[0], a.fixed_e);
+      write_count(a, p1, count[1], a.fixed_e);
+    }
   } else {
-    if (s0 == 0) filter_and_write<W, 2>(a, p0, x0);
-    if (s1 == 0) filter_and_write<W, 2>(a, p1, x1);
+    if (s0 == 0) filter_and_write<W, VARIANT>(a, p0, x0);
+    if (s1 == 0) filter_and_write<W, VARIANT>(a, p1, x1);
   }
 }
 
@@ -747,10 +826,10 @@ cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
   if (a.compact == 0) {
     // Two pairs per thread only while it keeps 3 blocks per SM (W <= 4): at
     // W = 5 (2 blocks) it measured 40% slower at e = 2, 150 bp.
-    if constexpr (VARIANT == 2 && W <= 4) {
+    if constexpr ((VARIANT == 2 || VARIANT == 3) && W <= 4) {
       if (a.m > 0) {
         const uint64_t threads = (a.n_pairs + 1) / 2;
-        filter_pair2_kernel<W><<<(unsigned)((threads + kFilterThreads - 1) / kFilterThreads), kFilterThreads, 0,
+        filter_pair2_kernel<W, VARIANT><<<(unsigned)((threads + kFilterThreads - 1) / kFilterThreads), kFilterThreads, 0,
                                  stream>>>(a);
         return cudaGetLastError();
       }

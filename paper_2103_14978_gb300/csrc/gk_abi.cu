@@ -40,6 +40,7 @@ int cuda_check(cudaError_t err, const char *what) {
 // Variant of the per-pair code for a launch: 2 deferred erosion, 1 exact
 // with every shift below 32, 0 exact for any thresholds.
 int filter_variant(const FilterArgs &a) {
+  if (a.out_stride != 0) return 3;  // a threshold sweep (gk_filter_sweep)
   // Every shift count below 32 (one threshold under 32, or reads of at most
   // 32 bases): the edge vectors live in the end words only.
   const bool small = (!a.pair_e && a.fixed_e < 32) || a.m <= 32;
@@ -271,6 +272,62 @@ int gk_filter(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64
   a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 &&
                (pair_e || (n_dense && fixed_e >= e_queue))) ? 1 : 0;
   return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter: launch");
+}
+
+int gk_filter_sweep(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words, uint64_t n_reads,
+                    const uint8_t *read_nflag, uint32_t m, const uint32_t *pair_read, const uint32_t *pair_off,
+                    uint32_t e_lo, uint32_t e_hi, uint64_t n_pairs, int count_mode, uint32_t flags,
+                    uint8_t *accept_out, uint16_t *edits_out, uint64_t out_stride, uint32_t *err_count,
+                    void *stream) {
+  gk::clear_error();
+  if (!ref) return fail(GK_EINVAL, "gk_filter_sweep: null reference handle");
+  if (m > GK_MAX_LEN) return fail(GK_ERANGE, "gk_filter_sweep: m above GK_MAX_LEN");
+  if (e_lo > e_hi) return fail(GK_EINVAL, "gk_filter_sweep: e_lo > e_hi");
+  if (e_hi > 255) return fail(GK_ERANGE, "gk_filter_sweep: e_hi above 255");
+  if (m > 0 && (e_hi < m - 1 ? e_hi : m - 1) > GK_SWEEP_MAX_SHIFT)
+    return fail(GK_ERANGE, "gk_filter_sweep: min(e_hi, m-1) above GK_SWEEP_MAX_SHIFT");
+  if (n_pairs == 0) return GK_OK;
+  if (n_pairs > kMaxPairs) return fail(GK_ERANGE, "gk_filter_sweep: too many pairs for one launch");
+  const bool result_byte = (flags & GK_FLAG_RESULT_BYTE) != 0;
+  if (flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE)) return fail(GK_EINVAL, "gk_filter_sweep: unknown flags");
+  if (flags & GK_FLAG_NO_EDGE_FIX)
+    return fail(GK_EINVAL, "gk_filter_sweep: computes the Sec. 3.4 edge OR only (use gk_filter without it)");
+  if (result_byte && e_hi > 252) return fail(GK_ERANGE, "gk_filter_sweep: GK_FLAG_RESULT_BYTE needs e_hi <= 252");
+  if (!pair_read || !pair_off || !accept_out || (!edits_out && !result_byte))
+    return fail(GK_EINVAL, "gk_filter_sweep: null pair or output buffer");
+  if (out_stride < n_pairs) return fail(GK_EINVAL, "gk_filter_sweep: out_stride < n_pairs");
+  const uint32_t W = m == 0 ? 1 : (m + 31) / 32;
+  if (m > 0 && (!reads || stride_words < W))
+    return fail(GK_EINVAL, "gk_filter_sweep: reads missing or stride_words < ceil(m/32)");
+  if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
+    return fail(GK_EINVAL, "gk_filter_sweep: unknown count_mode");
+  if (reads && !aligned(reads, 8)) return fail(GK_EINVAL, "gk_filter_sweep: reads must be 8-byte aligned");
+  gk::FilterArgs a{};
+  a.ref_hl = ref->hl;
+  a.ref_nidx = ref->nidx;
+  a.ref_len = ref->n_bases;
+  a.reads = reinterpret_cast<const uint2 *>(reads);
+  a.stride_words = stride_words;
+  a.n_reads = n_reads;
+  a.read_nflag = read_nflag;
+  a.m = m;
+  a.pair_read = pair_read;
+  a.pair_off = pair_off;
+  a.fixed_e = e_lo;
+  a.sweep_hi = e_hi;
+  a.out_stride = out_stride;
+  a.n_pairs = n_pairs;
+  a.count_mode = count_mode;
+  a.edge_on = 1;
+  a.result_byte = result_byte ? 1 : 0;
+  a.accept = accept_out;
+  a.edits = edits_out;
+  a.err_count = err_count;
+  // As gk_filter: with a genome dense in N, persistent warps filter only
+  // the defined pairs (a sweep is work enough to repay the queueing).
+  const bool n_dense = (double)ref->n_undefined * (double)m >= 0.05 * (double)ref->n_bases;
+  a.compact = (ref->n_undefined > 0 && n_pairs < (1ull << 32) && m > 0 && n_dense) ? 1 : 0;
+  return gk::cuda_check(gk::launch_filter((int)W, a, (cudaStream_t)stream), "gk_filter_sweep: launch");
 }
 
 int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride, uint64_t n_reads, uint32_t m,

@@ -61,6 +61,11 @@ struct FilterArgs {
   uint32_t *err_count;  // nullable
   int compact;          // plain filter: persistent warps that filter only defined pairs
   int result_byte;      // accept receives one result byte per pair (GK_FLAG_RESULT_BYTE)
+  // Threshold sweep (gk_filter_sweep): thresholds fixed_e .. sweep_hi, the
+  // results of threshold e at accept / edits + (e - fixed_e) * out_stride;
+  // sweep_hi < fixed_e: one threshold.
+  uint32_t sweep_hi;
+  uint64_t out_stride;
 };
 
 // Launches the plain filter for words-per-read W = ceil(m/32) (1..16).

@@ -114,7 +114,7 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
     return gk::fail(GK_EINVAL, "gk_pipe_create: n_thresholds must be 1..64 with a threshold array");
   if (d->count_mode != GK_COUNT_RUNS4 && d->count_mode != GK_COUNT_POPCOUNT)
     return gk::fail(GK_EINVAL, "gk_pipe_create: unknown count_mode");
-  if (d->flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE))
+  if (d->flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE | GK_PIPE_SLICED))
     return gk::fail(GK_EINVAL, "gk_pipe_create: unknown flags");
   if (d->flags & GK_FLAG_RESULT_BYTE)
     for (uint32_t i = 0; i < d->n_thresholds; ++i)
@@ -136,12 +136,13 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
   p->n_slots = d->n_slots;
   p->thresholds.assign(d->thresholds, d->thresholds + d->n_thresholds);
   p->count_mode = d->count_mode;
-  p->flags = d->flags;
+  p->flags = d->flags & ~GK_PIPE_SLICED;  // the filters' flags
   const uint64_t n_th = d->n_thresholds;
-  // The bit-sliced filter when it covers the pipe's read length and every
-  // threshold (edge OR on, min(e, m-1) within the compiled shift counts).
-  bool slice = !(d->flags & GK_FLAG_NO_EDGE_FIX) && d->read_len >= 1 && d->read_len <= GK_SLICED_MAX_LEN &&
-               d->max_pairs > 0;
+  // The bit-sliced filter when the pipe asks for it (GK_PIPE_SLICED) and it
+  // covers the read length and every threshold (edge OR on, min(e, m-1)
+  // within the compiled shift counts).
+  bool slice = (d->flags & GK_PIPE_SLICED) && !(d->flags & GK_FLAG_NO_EDGE_FIX) && d->read_len >= 1 &&
+               d->read_len <= GK_SLICED_MAX_LEN && d->max_pairs > 0;
   for (uint32_t i = 0; slice && i < d->n_thresholds; ++i)
     slice = (d->thresholds[i] < d->read_len - 1 ? d->thresholds[i] : d->read_len - 1) <= GK_SLICED_MAX_SHIFT;
   p->sliced_cap = slice ? gk_sliced_bytes(d->max_pairs, d->read_len) : 0;
@@ -215,18 +216,31 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
   for (uint64_t i = 0; i < n_th && n_pairs;) {
-    // Sliced: every run of consecutive thresholds (e, e+1, ...) is one sweep.
+    // Every run of consecutive thresholds (e, e+1, ...) is one sweep launch
+    // when the sweep covers it (edge OR on, shift counts within the
+    // sweep's limit), sliced when the pipe slices, per pair otherwise.
+    const bool sweep_ok = !(p->flags & GK_FLAG_NO_EDGE_FIX);
     uint64_t j = i;
+    if (sweep_ok || p->sliced_cap)
+      while (j + 1 < n_th && p->thresholds[j + 1] == p->thresholds[j] + 1 &&
+             (p->sliced_cap || (p->thresholds[j + 1] < p->read_len - 1 ? p->thresholds[j + 1] : p->read_len - 1) <=
+                                   GK_SWEEP_MAX_SHIFT))
+        ++j;
+    const uint32_t ki = p->thresholds[i] < p->read_len - 1 ? p->thresholds[i] : p->read_len - 1;
+    int rc;
     if (p->sliced_cap)
-      while (j + 1 < n_th && p->thresholds[j + 1] == p->thresholds[j] + 1) ++j;
-    const int rc =
-        p->sliced_cap
-            ? gk_filter_sliced_sweep(s.sliced, p->sliced_cap, n_pairs, p->read_len, p->thresholds[i],
-                                     p->thresholds[j], p->count_mode, p->flags, s.accept + i * n_pairs,
-                                     result_byte ? nullptr : s.edits + i * n_pairs, n_pairs, nullptr, p->s_run)
-            : gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read, s.pair_off,
-                        nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags, s.accept + i * n_pairs,
-                        result_byte ? nullptr : s.edits + i * n_pairs, nullptr, p->s_run);
+      rc = gk_filter_sliced_sweep(s.sliced, p->sliced_cap, n_pairs, p->read_len, p->thresholds[i], p->thresholds[j],
+                                  p->count_mode, p->flags, s.accept + i * n_pairs,
+                                  result_byte ? nullptr : s.edits + i * n_pairs, n_pairs, nullptr, p->s_run);
+    else if (sweep_ok && ki <= GK_SWEEP_MAX_SHIFT)
+      rc = gk_filter_sweep(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read, s.pair_off,
+                           p->thresholds[i], p->thresholds[j], n_pairs, p->count_mode, p->flags,
+                           s.accept + i * n_pairs, result_byte ? nullptr : s.edits + i * n_pairs, n_pairs, nullptr,
+                           p->s_run);
+    else
+      rc = gk_filter(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read, s.pair_off,
+                     nullptr, p->thresholds[i], n_pairs, p->count_mode, p->flags, s.accept + i * n_pairs,
+                     result_byte ? nullptr : s.edits + i * n_pairs, nullptr, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
     i = j + 1;
   }

@@ -19,6 +19,7 @@ GK_OK, GK_EINVAL, GK_ERANGE, GK_ENOMEM, GK_ECUDA = 0, -1, -2, -3, -4
 GK_COUNT_RUNS4, GK_COUNT_POPCOUNT = 0, 1
 GK_FLAG_NO_EDGE_FIX = 1
 GK_FLAG_RESULT_BYTE = 2
+GK_PIPE_SLICED = 4
 GK_RESULT_MAX_COUNT, GK_RESULT_UNDEFINED, GK_RESULT_INVALID = 253, 254, 255
 GK_EDITS_UNDEFINED, GK_EDITS_INVALID = 0xFFFF, 0xFFFE
 
@@ -49,6 +50,9 @@ _SIGS = {
     "gk_filter": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_uint32,
                    _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int,
                    _c.c_uint32, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "gk_filter_sweep": ([_c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p, _c.c_uint32,
+                         _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint32, _c.c_uint64, _c.c_int, _c.c_uint32,
+                         _c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_filter_ascii": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_uint64, _c.c_uint32, _c.c_void_p,
                          _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_int, _c.c_uint32, _c.c_void_p,
                          _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
@@ -84,6 +88,7 @@ _SIGS = {
 GK_NOALLOC_MAX_PAIRS = 1_000_000
 GK_SLICED_MAX_LEN = 255
 GK_SLICED_MAX_SHIFT = 15
+GK_SWEEP_MAX_SHIFT = 30
 GK_GATHER_MAX_BYTES = 65536
 
 
@@ -264,6 +269,39 @@ def gk_filter(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: i
     return accept, (None if result_byte else edits)
 
 
+def gk_filter_sweep(ref: Reference, reads: torch.Tensor, stride_words: int, n_reads: int,
+                    read_nflag: torch.Tensor | None, m: int, pair_read: torch.Tensor, pair_off: torch.Tensor,
+                    e_lo: int, e_hi: int, count_mode: int = GK_COUNT_RUNS4, flags: int = 0,
+                    accept: torch.Tensor | None = None, edits: torch.Tensor | None = None,
+                    out_stride: int | None = None, err_count: torch.Tensor | None = None, stream=None):
+    """gk_filter at every threshold e_lo..e_hi in one launch
+    (gk_filter_sweep).  Returns (accept, edits) as views of shape
+    (e_hi - e_lo + 1, n_pairs) over threshold-major buffers (rows out_stride
+    elements apart), or (result bytes, None) with GK_FLAG_RESULT_BYTE."""
+    n = pair_read.numel()
+    dev = pair_read.device
+    result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
+    n_e = int(e_hi) - int(e_lo) + 1
+    if out_stride is None:
+        out_stride = max(-(-n // 16) * 16, 1)
+    need = (n_e - 1) * out_stride + n if n_e > 0 else 0
+    if accept is None:
+        accept = torch.empty(max(need, n_e * out_stride, 1), dtype=torch.uint8, device=dev)
+    if edits is None and not result_byte:
+        edits = torch.empty(max(need, n_e * out_stride, 1), dtype=torch.int16, device=dev)
+    if m > 0 and reads.numel() < n_reads * stride_words * 2:
+        raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
+    _check(lib().gk_filter_sweep(
+        ref.handle, _dptr(reads, torch.int32, "reads"), stride_words, n_reads,
+        _dptr(read_nflag, torch.uint8, "read_nflag", n_reads), m, _dptr(pair_read, torch.int32, "pair_read"),
+        _dptr(pair_off, torch.int32, "pair_off", n), int(e_lo), int(e_hi), n, count_mode, flags,
+        _dptr(accept, torch.uint8, "accept", need),
+        None if result_byte else _dptr(edits, torch.int16, "edits", need), out_stride,
+        _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
+    rows = lambda t: t.as_strided((n_e, n), (out_stride, 1))  # noqa: E731
+    return rows(accept), (None if result_byte else rows(edits))
+
+
 def gk_filter_ascii(ref: Reference, ascii: torch.Tensor, ascii_stride: int, n_reads: int, m: int,
                     pair_read: torch.Tensor, pair_off: torch.Tensor, e, count_mode: int = GK_COUNT_RUNS4,
                     flags: int = 0, accept: torch.Tensor | None = None, edits: torch.Tensor | None = None,
@@ -356,11 +394,11 @@ def gk_filter_sliced_sweep(sliced: torch.Tensor, n_pairs: int, m: int, e_lo: int
     n_e = int(e_hi) - int(e_lo) + 1
     if out_stride is None:
         out_stride = -(-n_pairs // 16) * 16
-    if accept is None:
-        accept = torch.empty(max(n_e, 1) * out_stride, dtype=torch.uint8, device=dev)
-    if edits is None and not result_byte:
-        edits = torch.empty(max(n_e, 1) * out_stride, dtype=torch.int16, device=dev)
     need = (n_e - 1) * out_stride + n_pairs if n_e > 0 else 0
+    if accept is None:
+        accept = torch.empty(max(need, n_e * out_stride, 1), dtype=torch.uint8, device=dev)
+    if edits is None and not result_byte:
+        edits = torch.empty(max(need, n_e * out_stride, 1), dtype=torch.int16, device=dev)
     _check(lib().gk_filter_sliced_sweep(
         _dptr(sliced, torch.uint8, "sliced"), sliced.numel(), n_pairs, m, int(e_lo), int(e_hi), count_mode,
         flags, _dptr(accept, torch.uint8, "accept", need),

@@ -149,6 +149,8 @@ def test_sliced_sizes_and_host_checks(libgk):
     assert b"gk_filter_sliced" in L.gk_last_error()
     assert L.gk_filter_sliced(buf, cap, 0, 100, 3, 0, 0, None, None, None) == libgk.GK_OK  # nothing to do
     assert L.gk_slice(None, None, 4, 1, None, 100, None, None, 64, buf, cap, None, None) == E  # no reference
+    fs = L.gk_filter_sweep
+    assert fs(None, None, 4, 1, None, 100, buf, buf, 0, 3, 64, 0, 0, buf, buf, 64, None, None) == E  # no reference
     sw = L.gk_filter_sliced_sweep
     assert sw(buf, cap, 64, 100, 0, 16, 0, 0, buf, buf, 64, None, None) == R  # min(e_hi, m-1) > 15
     assert sw(buf, cap, 64, 100, 5, 4, 0, 0, buf, buf, 64, None, None) == E  # e_lo > e_hi

@@ -29,10 +29,14 @@ def pinned(a: np.ndarray) -> torch.Tensor:
     return t
 
 
-@pytest.mark.parametrize("n_slots,ths", [(2, THRESHOLDS), (3, THRESHOLDS), (4, THRESHOLDS), (3, (1, 12))])
-def test_pipe_batches_equal_the_oracle(n_slots, ths):
-    """Thresholds within the sliced filter's shift counts take gk_slice +
-    gk_filter_sliced; a set with e = 12 takes gk_filter."""
+@pytest.mark.parametrize("n_slots,ths,flags", [(2, THRESHOLDS, 0), (3, THRESHOLDS, 0), (4, THRESHOLDS, 0),
+                                               (3, (1, 12), 0), (3, (0, 1, 2, 5, 6, 7, 29, 30, 31, 40), 0),
+                                               (3, THRESHOLDS, 4), (2, (1, 12), 4)])
+def test_pipe_batches_equal_the_oracle(n_slots, ths, flags):
+    """Runs of consecutive thresholds take one gk_filter_sweep each (shift
+    counts up to 30), thresholds above it gk_filter; with GK_PIPE_SLICED
+    (flags 4) gk_slice + gk_filter_sliced_sweep where the sliced filter
+    covers the set, gk_filter otherwise."""
     require_gpu()
     THRESHOLDS = ths
     w = synth.config2(scale=0.001, ref_bases=2_000_000)
@@ -42,7 +46,7 @@ def test_pipe_batches_equal_the_oracle(n_slots, ths):
     max_reads = max(b[1] for b in bs)
     max_pairs = max(b[2].size for b in bs)
     want = {e: oracle_run(w, e) for e in THRESHOLDS}
-    with gk.Pipe(ref, max_reads, w.stride, 100, max_pairs, THRESHOLDS, n_slots=n_slots) as pipe:
+    with gk.Pipe(ref, max_reads, w.stride, 100, max_pairs, THRESHOLDS, n_slots=n_slots, flags=flags) as pipe:
         jobs = []
         for asc, nr, pr, po, idx in bs:
             acc = torch.empty(len(THRESHOLDS) * pr.size, dtype=torch.uint8).pin_memory()
