@@ -242,36 +242,19 @@ __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const Pai
 // the window and on which window bases are 'A', so their corrections for all
 // k are computed once per pair; so are the two values of the AND one base
 // outside each end that the final erosion reads.
-template <int W, int NP>
-__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t m, uint32_t K, uint32_t tail,
-                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
-                                                const uint32_t (&rh)[W], const uint32_t (&rl)[W],
-                                                const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
-                                                uint32_t (&count)[NP]);
-
 // Deferred-erosion counts of NP pairs that share one read and one shift
 // count K, each against its own window: the read's +k and -k copies (4W
 // funnel shifts per step) are built once for all NP windows.  rh/rl and
 // gh/gl are the read's and the windows' planes, zero past m.
-//
-// SWEEP: the counts of every shift count K = Klo .. K (a threshold sweep):
-// the 2k+1 masks of shift count k are those of k-1 and the two shifted by k,
-// so the running AND after step k is the AND of K = k, and the once-per-pair
-// finish (end values, erosion, corrections, count) runs on it at each k from
-// Klo on; emit(k, count) receives each.  Without SWEEP the finish runs once,
-// for K, into count.
-template <int W, int NP, bool SWEEP = false, typename Emit = int>
+template <int W, int NP>
 __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m, uint32_t K,
                                                 const uint32_t (&rh)[W], const uint32_t (&rl)[W],
                                                 const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
-                                                uint32_t (&count)[NP], uint32_t Klo = 0, Emit emit = 0) {
+                                                uint32_t (&count)[NP]) {
   const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
   const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
 
   uint32_t acc[NP][W], d[W], dn[W];
-  auto finish = [&](uint32_t Kf) {
-    deferred_finish<W, NP>(a, m, Kf, tail, lastmask, acc, rh, rl, gh, gl, count);
-  };
   // dilation of a mask: bit i <- d[i-1] | d[i] | d[i+1], zeros outside the words
   auto dil = [&](const uint32_t (&dd)[W], int w) -> uint32_t {
     const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
@@ -284,12 +267,6 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[j][w]) | (rl[w] ^ gl[j][w]);
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[j][w] = dil(d, w);  // shift 0
-  }
-  if constexpr (SWEEP) {
-    if (Klo == 0) {
-      finish(0);
-      emit(0u, count);
-    }
   }
   {
     uint32_t ph[W], pl[W], nh[W], nl[W];
@@ -331,26 +308,9 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
 #pragma unroll
         for (int w = 0; w < W; ++w) acc[j][w] &= dil(d, w) & dil(dn, w);
       }
-      if constexpr (SWEEP) {
-        if (k >= Klo) {
-          finish(k);
-          emit(k, count);
-        }
-      }
     }
   }
-  if constexpr (!SWEEP) finish(K);
-}
 
-// The once-per-pair end of deferred_counts for shift count K: the AND's
-// values one base outside each end, the erosion, the corrections next to the
-// vacated runs and the count (acc is read, not changed).
-template <int W, int NP>
-__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t m, uint32_t K, uint32_t tail,
-                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
-                                                const uint32_t (&rh)[W], const uint32_t (&rl)[W],
-                                                const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
-                                                uint32_t (&count)[NP]) {
   // ---- once per pair: end values of the AND, corrections, final erosion ----
   const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
   const uint32_t r1k = rangeK & ~1u;       // bits 1..K
@@ -407,6 +367,215 @@ __device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t m,
       const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
       const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
       const uint32_t nc = __brev((~(c1 & c2) & r1k) | ((~c2 & r1k) << 1));  // bit b: position m-32+b
+      f[W - 1] &= ~(nc >> (32u - tail));
+      if (W >= 2 && tail < 32) f[W >= 2 ? W - 2 : 0] &= ~(nc << tail);
+    }
+    f[W - 1] &= lastmask;
+
+    uint32_t c = 0;
+    if (a.count_mode == GK_COUNT_POPCOUNT) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) c += __popc(f[w]);
+    } else {
+#pragma unroll
+      for (int w = 0; w < W; ++w) c += __popc(f[w] & ~((f[w] << 1) & 0xEEEEEEEEu));
+    }
+    count[j] = c;
+  }
+}
+
+template <int NP>
+struct FinishPrep;
+template <int W, int NP>
+__device__ __forceinline__ void deferred_prep(int j, uint32_t tail, uint32_t lastmask, const uint32_t (&rh)[W],
+                                              const uint32_t (&rl)[W], const uint32_t (&gh)[NP][W],
+                                              const uint32_t (&gl)[NP][W], FinishPrep<NP> &pr);
+template <int W, int NP>
+__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t K, uint32_t tail,
+                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
+                                                const FinishPrep<NP> &pr, uint32_t (&count)[NP]);
+
+// deferred_counts at every shift count K = Klo .. K of a threshold sweep in
+// one pass: the 2k+1 masks of shift count k are those of k-1 and the two
+// shifted by k, so the running AND after step k is the AND of shift count k,
+// and the once-per-pair finish (end values, erosion, corrections, count)
+// runs on it at each k from Klo on; emit(k, count) receives the counts.  The
+// finish's shift-independent terms are prepared once per pair.
+template <int W, int NP, typename Emit>
+__device__ __forceinline__ void deferred_sweep_counts(const FilterArgs &a, uint32_t m, uint32_t K,
+                                                      const uint32_t (&rh)[W], const uint32_t (&rl)[W],
+                                                      const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
+                                                      uint32_t (&count)[NP], uint32_t Klo, Emit emit) {
+  const uint32_t tail = m - 32u * (W - 1);  // 1..32 bases in the last word
+  const uint32_t lastmask = tail >= 32 ? 0xffffffffu : ((1u << tail) - 1u);
+
+  uint32_t acc[NP][W], d[W], dn[W];
+  FinishPrep<NP> pr;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) deferred_prep<W, NP>(j, tail, lastmask, rh, rl, gh, gl, pr);
+  auto finish = [&](uint32_t Kf) { deferred_finish<W, NP>(a, Kf, tail, lastmask, acc, pr, count); };
+  // dilation of a mask: bit i <- d[i-1] | d[i] | d[i+1], zeros outside the words
+  auto dil = [&](const uint32_t (&dd)[W], int w) -> uint32_t {
+    const uint32_t below = __funnelshift_l(w > 0 ? dd[w - 1] : 0u, dd[w], 1);
+    const uint32_t above = __funnelshift_r(dd[w], w + 1 < W ? dd[w + 1] : 0u, 1);
+    return dd[w] | below | above;
+  };
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) d[w] = (rh[w] ^ gh[j][w]) | (rl[w] ^ gl[j][w]);
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[j][w] = dil(d, w);  // shift 0
+  }
+  if (Klo == 0) {
+    finish(0);
+    emit(0u, count);
+  }
+  {
+    uint32_t ph[W], pl[W], nh[W], nl[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      ph[w] = nh[w] = rh[w];
+      pl[w] = nl[w] = rl[w];
+    }
+    // The vacated positions of each shifted mask are ORed into its difference
+    // vector before the dilation: dil(d | V) = dil(d) | dil(V), the mask ORed
+    // with its dilated vacated set.
+    uint32_t lead = 0u;               // mask +k: positions 0..k-1 (word 0)
+    uint32_t tv_hi = ~lastmask;       // mask -k: positions >= m-k (and >= m), top word
+    uint32_t tv_lo = 0u;              // and the word below it
+    for (uint32_t k = 1; k <= K; ++k) {
+#pragma unroll
+      for (int w = W - 1; w >= 0; --w) {
+        ph[w] = __funnelshift_l(w > 0 ? ph[w - 1] : 0u, ph[w], 1);
+        pl[w] = __funnelshift_l(w > 0 ? pl[w - 1] : 0u, pl[w], 1);
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
+        nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
+      }
+      lead = 2u * lead + 1u;
+      tv_lo = __funnelshift_r(tv_lo, tv_hi, 1);
+      tv_hi = __funnelshift_r(tv_hi, 0xffffffffu, 1);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const uint32_t vp = w == 0 ? lead : 0u;
+          const uint32_t vn = w == W - 1 ? tv_hi : (w == W - 2 ? tv_lo : 0u);
+          d[w] = (ph[w] ^ gh[j][w]) | vp | (pl[w] ^ gl[j][w]);
+          dn[w] = (nh[w] ^ gh[j][w]) | vn | (nl[w] ^ gl[j][w]);
+        }
+        d[W - 1] &= lastmask;  // the +k copy carries read bases past m
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j][w] &= dil(d, w) & dil(dn, w);
+      }
+      if (k >= Klo) {
+        finish(k);
+        emit(k, count);
+      }
+    }
+  }
+}
+
+// The shift-count-independent terms of the once-per-pair end: per pair, the
+// compare of window base 0 with the read's first bases (the AND one base
+// below position 0), of window base m-1 with the read's last bases (the AND
+// one base above m-1, when m fills the words), and the correction words at
+// both ends before they are limited to the positions of a shift count.
+template <int NP>
+struct FinishPrep {
+  uint32_t q0[NP], qm[NP];
+  uint32_t lx[NP], ly[NP];  // low end: bit p set where a correction clears position p (from mask p) / p+1 (mask p)
+  uint32_t hx[NP], hy[NP];  // high end, mirrored (bit j: position m-1-j), bit-reversed
+};
+
+// The high-end words are kept bit-reversed, so that each finish reverses one
+// mask instead of one word per pair.
+template <int W, int NP>
+__device__ __forceinline__ void deferred_prep(int j, uint32_t tail, uint32_t lastmask, const uint32_t (&rh)[W],
+                                              const uint32_t (&rl)[W], const uint32_t (&gh)[NP][W],
+                                              const uint32_t (&gl)[NP][W], FinishPrep<NP> &pr) {
+  // The read's last 32 bases mirrored: bit j is position m-1-j (positions
+  // below 0 read as code 00).  The high end's terms are the low end's
+  // formulas on mirrored vectors, in 32-bit words.
+  const uint32_t xrh = __funnelshift_rc(W >= 2 ? rh[W >= 2 ? W - 2 : 0] : 0u, rh[W - 1], tail);
+  const uint32_t xrl = __funnelshift_rc(W >= 2 ? rl[W >= 2 ? W - 2 : 0] : 0u, rl[W - 1], tail);
+  const uint32_t b0h = 0u - (xrh >> 31), b0l = 0u - (xrl >> 31);                // R[m-1]
+  const uint32_t b1h = 0u - ((xrh >> 30) & 1u), b1l = 0u - ((xrl >> 30) & 1u);  // R[m-2]
+  const uint32_t r0h = 0u - (rh[0] & 1u), r0l = 0u - (rl[0] & 1u);              // R[0]
+  const uint32_t r1h = 0u - ((rh[0] >> 1) & 1u), r1l = 0u - ((rl[0] >> 1) & 1u);  // R[1]
+  {
+    // Window base 0 against R[i] (bit i), every non-positive shift.
+    const uint32_t g0h = 0u - (gh[j][0] & 1u), g0l = 0u - (gl[j][0] & 1u);
+    pr.q0[j] = (rh[0] ^ g0h) | (rl[0] ^ g0l);
+    // The window's last 32 bases mirrored.
+    const uint32_t mgh = __brev(__funnelshift_rc(W >= 2 ? gh[j][W >= 2 ? W - 2 : 0] : 0u, gh[j][W - 1], tail));
+    const uint32_t mgl = __brev(__funnelshift_rc(W >= 2 ? gl[j][W >= 2 ? W - 2 : 0] : 0u, gl[j][W - 1], tail));
+    // Window base m-1 against R[m-1-i] (bit i), every non-negative shift;
+    // used only when m fills the words.
+    pr.qm[j] = 0u;
+    if (tail == 32) {
+      const uint32_t gmh = 0u - (mgh & 1u), gml = 0u - (mgl & 1u);
+      pr.qm[j] = (__brev(xrh) ^ gmh) | (__brev(xrl) ^ gml);
+    }
+    {  // low end (positions 1..K+1, word 0)
+      const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
+      const uint32_t a0 = (gh[j][0] ^ r0h) | (gl[j][0] ^ r0l);
+      const uint32_t a1 = ((gh[j][0] ^ r1h) | (gl[j][0] ^ r1l)) & v0;
+      const uint32_t vac = gh[j][0] | gl[j][0];
+      const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
+      const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
+      pr.lx[j] = ~(c1 & c2);
+      pr.ly[j] = ~c2;
+    }
+    {  // high end (positions m-K-2..m-2), mirrored; kept bit-reversed
+      const uint32_t a0 = (mgh ^ b0h) | (mgl ^ b0l);
+      const uint32_t a1 = (mgh ^ b1h) | (mgl ^ b1l);
+      const uint32_t vac = mgh | mgl;
+      const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
+      const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
+      pr.hx[j] = __brev(~(c1 & c2));
+      pr.hy[j] = __brev(~c2);
+    }
+  }
+}
+
+// The once-per-pair end of deferred_sweep_counts for shift count K: the
+// AND's values one base outside each end, the erosion, the corrections next
+// to the vacated runs and the count (acc is read, not changed), as at the end
+// of deferred_counts.
+template <int W, int NP>
+__device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t K, uint32_t tail,
+                                                uint32_t lastmask, const uint32_t (&acc)[NP][W],
+                                                const FinishPrep<NP> &pr, uint32_t (&count)[NP]) {
+  // ---- once per pair: end values of the AND, corrections, final erosion ----
+  const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
+  const uint32_t r1k = rangeK & ~1u;       // bits 1..K
+  const uint32_t r1kr = __brev(r1k);       // the same, mirrored
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    // AND one base below position 0: every non-positive shift compares G[0]
+    // with R[i], i = 0..K.
+    const uint32_t vlo = ((~pr.q0[j] & rangeK) == 0) ? 1u : 0u;
+    // AND one base above position m-1, needed only when m fills the words:
+    // every non-negative shift compares G[m-1] with R[m-1-i], i = 0..K.
+    uint32_t vtop = 0u;
+    if (tail == 32) vtop = ((~pr.qm[j] & rangeK) == 0) ? 1u : 0u;
+    uint32_t f[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t lo_in = w > 0 ? acc[j][w - 1] : (vlo << 31);
+      const uint32_t hi_in = w + 1 < W ? acc[j][w + 1] : vtop;
+      f[w] = acc[j][w] & __funnelshift_l(lo_in, acc[j][w], 1) & __funnelshift_r(acc[j][w], hi_in, 1);
+    }
+    // Low-end corrections (positions 1..K+1, word 0).
+    f[0] &= ~((pr.lx[j] & r1k) | ((pr.ly[j] & r1k) << 1));
+    // High-end corrections (positions m-K-2..m-2), mapped back from the
+    // mirrored words: bit b of nc is position m-32+b.
+    {
+      const uint32_t nc = (pr.hx[j] & r1kr) | ((pr.hy[j] & r1kr) >> 1);
       f[W - 1] &= ~(nc >> (32u - tail));
       if (W >= 2 && tail < 32) f[W >= 2 ? W - 2 : 0] &= ~(nc << tail);
     }
@@ -482,8 +651,10 @@ __device__ __forceinline__ int pair_status(const FilterArgs &a, const PairData<W
   return status;
 }
 
+// SWEEP (VARIANT 3): the outcome goes to the row of every threshold.
+template <bool SWEEP = false>
 __device__ __forceinline__ void write_trivial(const FilterArgs &a, uint64_t p, int status) {
-  const uint32_t rows = a.sweep_hi >= a.fixed_e ? a.sweep_hi - a.fixed_e + 1 : 1;  // every threshold of a sweep
+  const uint32_t rows = SWEEP ? a.sweep_hi - a.fixed_e + 1 : 1;
   for (uint32_t i = 0; i < rows; ++i) {
     const uint64_t q = p + i * a.out_stride;
     if (a.result_byte) {
@@ -515,7 +686,7 @@ __device__ __forceinline__ void sweep_and_write(const FilterArgs &a, uint64_t p,
   pair_planes<W>(x, rh, rl, gh[0], gl[0]);
   const uint32_t e_lo = a.fixed_e, e_hi = a.sweep_hi, kmax = x.m - 1;
   const uint32_t Klo = min(e_lo, kmax), Khi = min(e_hi, kmax);
-  deferred_counts<W, 1, true>(a, x.m, Khi, rh, rl, gh, gl, count, Klo, [&](uint32_t K, const uint32_t (&c)[1]) {
+  deferred_sweep_counts<W, 1>(a, x.m, Khi, rh, rl, gh, gl, count, Klo, [&](uint32_t K, const uint32_t (&c)[1]) {
     const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
     for (uint32_t e = first; e <= last; ++e) write_count(a, p + (uint64_t)(e - e_lo) * a.out_stride, c[0], e);
   });
@@ -629,7 +800,7 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
     if (!active) return;
     const int status = pair_status<W>(a, cur);
     if (status != 0 || a.m == 0) {
-      write_trivial(a, p, status);
+      write_trivial<VARIANT == 3>(a, p, status);
       return;
     }
     filter_and_write<W, VARIANT>(a, p, cur);
@@ -699,7 +870,7 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
         const unsigned bad = __ballot_sync(0xffffffffu, status == 2);
         if (bad && lane == 0) atomicAdd(a.err_count, (unsigned)__popc(bad));
       }
-      if (status > 0 && active) write_trivial(a, p, status == 3 ? 0 : status);
+      if (status > 0 && active) write_trivial<VARIANT == 3>(a, p, status == 3 ? 0 : status);
       const unsigned need = __ballot_sync(0xffffffffu, status == 0);
       if ((need >> lane) & 1u) {
         const uint32_t slot = qn + __popc(need & ((1u << lane) - 1u));
@@ -780,8 +951,8 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
   }
   const int s0 = act0 ? pair_status<W>(a, x0) : -1;
   const int s1 = act1 ? pair_status<W>(a, x1) : -1;
-  if (s0 > 0) write_trivial(a, p0, s0);
-  if (s1 > 0) write_trivial(a, p1, s1);
+  if (s0 > 0) write_trivial<VARIANT == 3>(a, p0, s0);
+  if (s1 > 0) write_trivial<VARIANT == 3>(a, p1, s1);
   if (s0 == 0 && s1 == 0 && x0.rid == x1.rid) {
     uint32_t rh[W], rl[W], gh[2][W], gl[2][W], count[2];
     pair_planes<W>(x0, rh, rl, gh[0], gl[0]);
@@ -799,13 +970,30 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
     }
     if constexpr (VARIANT == 3) {
       const uint32_t e_lo = a.fixed_e, e_hi = a.sweep_hi, kmax = a.m - 1;
-      deferred_counts<W, 2, true>(a, a.m, min(e_hi, kmax), rh, rl, gh, gl, count, min(e_lo, kmax),
+      // Pairs 2t and 2t+1 are adjacent in every row: one 2-byte and one
+      // 4-byte store per threshold when the rows keep that alignment.
+      const bool pack = (((uintptr_t)a.accept | (a.result_byte ? 0u : (uintptr_t)a.edits)) & 3u) == 0 &&
+                        (a.out_stride & 1u) == 0;
+      deferred_sweep_counts<W, 2>(a, a.m, min(e_hi, kmax), rh, rl, gh, gl, count, min(e_lo, kmax),
                                   [&](uint32_t K, const uint32_t (&c)[2]) {
                                     const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
                                     for (uint32_t e = first; e <= last; ++e) {
                                       const uint64_t o = (uint64_t)(e - e_lo) * a.out_stride;
-                                      write_count(a, p0 + o, c[0], e);
-                                      write_count(a, p1 + o, c[1], e);
+                                      if (pack) {
+                                        uint32_t b0, b1;
+                                        if (a.result_byte) {
+                                          b0 = min(c[0], GK_RESULT_MAX_COUNT);
+                                          b1 = min(c[1], GK_RESULT_MAX_COUNT);
+                                        } else {
+                                          b0 = c[0] <= e;
+                                          b1 = c[1] <= e;
+                                          *reinterpret_cast<uint32_t *>(a.edits + o + p0) = c[0] | (c[1] << 16);
+                                        }
+                                        *reinterpret_cast<uint16_t *>(a.accept + o + p0) = (uint16_t)(b0 | (b1 << 8));
+                                      } else {
+                                        write_count(a, p0 + o, c[0], e);
+                                        write_count(a, p1 + o, c[1], e);
+                                      }
                                     }
                                   });
     } else {

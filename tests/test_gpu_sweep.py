@@ -92,6 +92,14 @@ def test_sweep_rows_and_arguments():
         assert_same((a[i].cpu().numpy(), dd.edits_u16(e[i])), oracle_run(w, t), f"rows e={t}")
         gap = acc[i * stride + 1000:(i + 1) * stride].cpu().numpy()
         assert (gap == 0xAB).all()
+    # an odd row stride and rows off the 4-byte grid: one store per pair
+    acc.fill_(0xAB)
+    a, e = gk.gk_filter_sweep(run.ref, r.packed, r.stride_words, r.n_reads, r.nflag, 100, run.pairs.pair_read,
+                              run.pairs.pair_off, 2, 5, accept=acc[1:], edits=ed[1:], out_stride=1001)
+    torch.cuda.synchronize()
+    for i, t in enumerate(range(2, 6)):
+        assert_same((a[i].cpu().numpy(), dd.edits_u16(e[i])), oracle_run(w, t), f"odd rows e={t}")
+    assert acc[0].item() == 0xAB
     for bad in (dict(e_lo=5, e_hi=4), dict(e_lo=0, e_hi=31), dict(e_lo=0, e_hi=10, flags=gk.GK_FLAG_NO_EDGE_FIX),
                 dict(e_lo=0, e_hi=10, out_stride=999)):
         with pytest.raises(gk.GKError):
