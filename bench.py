@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--tune-seconds", type=float, default=8.0, help="autotuner budget (config 4)")
     ap.add_argument("--no-extra", action="store_true", help="config 2 only (no config 3/4/5 keys)")
     ap.add_argument("--level-seconds", type=float, default=10.0, help="arrival time per serving load level")
+    ap.add_argument("--round-pairs", type=int, default=32_000_000, help="pairs per serving round, at most")
     return ap.parse_args()
 
 
@@ -783,6 +784,8 @@ def run_mine(args):
 
 
 E2E_WINDOWS = 3
+E2E_MIN_STEPS = 100
+E2E_MIN_SECONDS = 1.0
 
 
 def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True):
@@ -818,7 +821,18 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
         pipe.wait(tickets[-1])
 
     run(2 * slots)  # every slot's buffers used once before the timed region
-    steps = max(3, min(args.steps, 30))
+    # Windows of at least E2E_MIN_STEPS steps and E2E_MIN_SECONDS each, sized
+    # from one short untimed run, so that one stall of the shared host link
+    # cannot move the median.
+    t_est = time.perf_counter()
+    run(2 * slots)
+    est_ms = (time.perf_counter() - t_est) * 1e3 / (2 * slots)
+    steps = max(E2E_MIN_STEPS, int(E2E_MIN_SECONDS * 1e3 / max(est_ms, 1e-3)) + 1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([steps], dtype=torch.int64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        steps = int(t.item())
     windows = []
     for _ in range(E2E_WINDOWS):
         torch.cuda.synchronize()
@@ -838,8 +852,9 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
     return {"value": whole_job_rate(n * len(E_SWEEP), world, steps, ms), "unit": "Gpairs/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": ms / steps,
             "windows_ms_per_step": [x / steps for x in windows],
-            "timing": f"median of {E2E_WINDOWS} back-to-back windows of {steps} steps, each the slowest rank's "
-                      f"wall clock (the host link is shared with the machine's other GPUs)",
+            "timing": f"median of {E2E_WINDOWS} back-to-back windows of {steps} steps (at least {E2E_MIN_STEPS} "
+                      f"steps and {E2E_MIN_SECONDS:g} s each), each the slowest rank's wall clock (the host link "
+                      f"is shared with the machine's other GPUs)",
             "path": "pinned host ASCII reads + pairs -> gk_pipe (copy-in, device encode + one gk_filter_sweep "
                     "over the thresholds, copy-out on three streams, 3 steps in flight) -> results in pinned "
                     "host memory",
@@ -1066,7 +1081,11 @@ def measure_c5(args) -> dict:
     ref = synth.reference()
     gkref = gk.gk_load_reference(ref)
     lengths, rates = (100, 150, 250), (0.02, 0.05, 0.10)
-    pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000)
+    # Requests arrive back to back in per-length pinned buffers (sequential
+    # cuts, rows at each length's own stride); the server has one lane per
+    # stride.
+    pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000, stride_words=None, sequential=True)
+    lanes = tuple(sorted({pool.by_len[m]["sw"] for m in lengths}))
     stream = torch.cuda.current_stream()
     per_combo = {}  # the plain filter on the mix, every (m, e) equally likely
     for m in lengths:
@@ -1078,14 +1097,14 @@ def measure_c5(args) -> dict:
         ed = torch.empty(n, dtype=torch.int16, device="cuda")
         for rate in rates:
             e = int(np.ceil(round(rate * m, 9)))
-            f = lambda: gk.gk_filter(gkref, packed, pool.sw, p["lens"][1].shape[0], nflag, m, pr, po, e,  # noqa
+            f = lambda: gk.gk_filter(gkref, packed, p["sw"], p["lens"][1].shape[0], nflag, m, pr, po, e,  # noqa
                                      accept=acc, edits=ed)
             f()
             per_combo[f"{m}bp_e{e}"] = n / (time_events(torch, f, 5, stream) * 1e-3)
     plain = 1.0 / np.mean([1.0 / v for v in per_combo.values()])
     lo, hi = 1_000, 1_000_000
     mean_size = (hi - lo) / np.log(hi / lo)
-    cfg = serve.ServeConfig(mem_cap_bytes=8 << 30, max_round_pairs=8_000_000, copy_results=False)
+    cfg = serve.ServeConfig(mem_cap_bytes=16 << 30, max_round_pairs=args.round_pairs, copy_results=False, lanes=lanes)
     ex = serve.GpuExecutor(gkref, cfg)
     skip = 1.0
 
@@ -1118,7 +1137,10 @@ def measure_c5(args) -> dict:
                       f"saturated throughput (measured first: arrivals at 1.5x the plain filter's capacity, "
                       f"completions counted until the arrivals stop); "
                       f"latency = arrival -> results on the host, over requests arriving after {skip:g} s",
-            "ring_read_slots": ex.n_read_slots, "ring_pair_slots": ex.n_pair_slots}
+            "lanes": [{"row_words": sw, "read_slots": nr, "pair_slots": npr} for sw, nr, npr in ex.lanes],
+            "copies_per_round_last": ex.copies_last_round,
+            "inputs": "requests received back to back into per-length pinned buffers (rows at each length's "
+                      "own stride); a round's copies merge per lane and array"}
 
 
 def run_config(args, which: str):

@@ -39,11 +39,12 @@ GK_MAX_WORDS = 16
 @dataclasses.dataclass
 class Request:
     """One request: ``packed`` uint32 reads as gk_encode writes them
-    (n_reads x stride_words x 2, the server's stride), ``nflag`` uint8 and
-    ``lens`` uint16 per read, ``pair_read`` uint32 ids relative to these
-    reads, ``pair_off`` uint32 genome offsets, one threshold ``e``.  For
-    asynchronous copies the arrays should live in pinned host memory.
-    ``arrival`` is the time (s, from the start of ``run``) the request arrives."""
+    (n_reads x stride_words x 2, the stride of one of the server's lanes),
+    ``nflag`` uint8 and ``lens`` uint16 per read, ``pair_read`` uint32 read
+    ids (id - ``read_base`` indexes these reads), ``pair_off`` uint32 genome
+    offsets, one threshold ``e``.  For asynchronous copies the arrays should
+    live in pinned host memory.  ``arrival`` is the time (s, from the start
+    of ``run``) the request arrives."""
 
     id: int
     packed: np.ndarray
@@ -65,14 +66,18 @@ class Request:
     accept: np.ndarray | None = None
     edits: np.ndarray | None = None
     ascii: np.ndarray | None = None  # the reads' ASCII rows, kept only for checking
+    read_base: int = 0  # pair_read - read_base indexes these reads (ids of a larger numbering)
+    lane: int = -1
 
-    @property
-    def n_reads(self) -> int:
-        return int(self.lens.shape[0])
-
-    @property
-    def n_pairs(self) -> int:
-        return int(self.pair_read.shape[0])
+    def __post_init__(self):
+        # Sizes and host addresses are read once here: the scheduler handles
+        # tens of thousands of requests a second.  n_reads, n_pairs and
+        # stride_words (packed words per read row) are plain attributes.
+        self.n_reads = int(self.lens.shape[0])
+        self.n_pairs = int(self.pair_read.shape[0])
+        self.stride_words = int(self.packed.size // (2 * self.n_reads)) if self.n_reads else 0
+        self.host_ptrs = tuple(int(x.__array_interface__["data"][0])
+                               for x in (self.packed, self.nflag, self.lens, self.pair_read, self.pair_off))
 
     def cancel(self) -> bool:
         """Cancel a request that has not been admitted yet."""
@@ -152,7 +157,9 @@ class FifoRing:
 
 @dataclasses.dataclass
 class ServeConfig:
-    stride_words: int = 8             # packed words per read (reads up to 32 x this)
+    stride_words: int = 8             # packed words per read (reads up to 32 x this), one lane
+    lanes: tuple | None = None        # several lanes: their row strides (words per read); a request
+                                      # goes to the lane of its own row stride
     max_read_len: int = 256
     pairs_per_read: float = 4.0       # expected candidates per read, to split the memory budget
     mem_fraction: float = 0.25        # share of the free device memory the rings may take
@@ -182,27 +189,42 @@ class Server:
     def __init__(self, executor, config: ServeConfig):
         self.ex = executor
         self.cfg = config
-        self.read_ring = FifoRing(executor.n_read_slots)
-        self.pair_ring = FifoRing(executor.n_pair_slots)
+        # One (stride, read ring, pair ring) per lane of the executor; an
+        # executor without lanes is one lane of the configured stride.
+        lanes = getattr(executor, "lanes", None) or [(config.stride_words, executor.n_read_slots,
+                                                     executor.n_pair_slots)]
+        self.lane_stride = [int(st) for st, _, _ in lanes]
+        self.read_rings = [FifoRing(nr) for _, nr, _ in lanes]
+        self.pair_rings = [FifoRing(npr) for _, _, npr in lanes]
+        self.read_ring, self.pair_ring = self.read_rings[0], self.pair_rings[0]
         self.rounds_launched = 0
         self.max_inflight_seen = 0
         self.coalesced = []  # requests per round
 
+    def lane_of(self, r: Request) -> int:
+        sw = r.stride_words if r.n_reads else self.lane_stride[0]
+        return self.lane_stride.index(sw) if sw in self.lane_stride else -1
+
     def fits_at_all(self, r: Request) -> bool:
-        return (r.n_reads <= self.read_ring.size and r.n_pairs <= self.pair_ring.size
+        lane = self.lane_of(r)
+        if lane < 0:
+            return False
+        return (r.n_reads <= self.read_rings[lane].size and r.n_pairs <= self.pair_rings[lane].size
                 and r.n_pairs <= self.cfg.max_round_pairs
-                and (r.max_len if r.max_len >= 0 else int(r.lens.max(initial=0))) <= self.cfg.max_read_len
-                and r.packed.size == r.n_reads * self.cfg.stride_words * 2 and 0 <= r.e <= 255)
+                and (r.max_len if r.max_len >= 0 else int(r.lens.max(initial=0))) <= min(
+                    self.cfg.max_read_len, 32 * self.lane_stride[lane])
+                and 0 <= r.e <= 255)
 
     def _admit(self, r: Request, now: float) -> bool:
-        rs = self.read_ring.alloc(r.n_reads)
+        lane = self.lane_of(r)
+        rs = self.read_rings[lane].alloc(max(r.n_reads, 1))
         if rs is None:
             return False
-        ps = self.pair_ring.alloc(r.n_pairs)
+        ps = self.pair_rings[lane].alloc(max(r.n_pairs, 1))
         if ps is None:
-            self.read_ring.undo_last()
+            self.read_rings[lane].undo_last()
             return False
-        r.read_slot, r.pair_slot, r.status, r.t_admit = rs, ps, "admitted", now
+        r.lane, r.read_slot, r.pair_slot, r.status, r.t_admit = lane, rs, ps, "admitted", now
         return True
 
     def run(self, requests: list, clock=time.perf_counter, idle_sleep: float = 20e-6,
@@ -272,8 +294,8 @@ class Server:
             if self.cfg.copy_results:
                 r.accept, r.edits = self.ex.results(r)
             r.status = "done"
-            self.read_ring.release_oldest()
-            self.pair_ring.release_oldest()
+            self.read_rings[r.lane].release_oldest()
+            self.pair_rings[r.lane].release_oldest()
         free_slots.append(rnd.slot)
 
 
@@ -315,8 +337,46 @@ def latency_summary(requests: list) -> dict:
             "device_p99_ms": float(np.percentile(dev, 99))}
 
 
+def merge_ranges(dst: np.ndarray, src: np.ndarray, nb: np.ndarray):
+    """merge_copies on int64 arrays, vectorized: every run of entries whose
+    destination and source both continue the previous entry becomes one."""
+    keep = nb > 0
+    dst, src, nb = dst[keep], src[keep], nb[keep]
+    if dst.shape[0] == 0:
+        return dst, src, nb
+    brk = np.ones(dst.shape[0], bool)
+    brk[1:] = (dst[1:] != dst[:-1] + nb[:-1]) | (src[1:] != src[:-1] + nb[:-1])
+    starts = np.flatnonzero(brk)
+    return dst[starts], src[starts], np.add.reduceat(nb, starts)
+
+
+def merge_copies(dst: list, src: list, nb: list):
+    """Copies (dst, src, bytes) with every run of back-to-back entries
+    (destination and source both continuing the previous entry) merged into
+    one; empty entries dropped.  Returns three uint64 arrays."""
+    md, ms, mn = [], [], []
+    for d, s_, n in zip(dst, src, nb):
+        if n == 0:
+            continue
+        if mn and md[-1] + mn[-1] == d and ms[-1] + mn[-1] == s_:
+            mn[-1] += n
+        else:
+            md.append(d)
+            ms.append(s_)
+            mn.append(n)
+    return np.array(md, np.uint64), np.array(ms, np.uint64), np.array(mn, np.uint64)
+
+
 class GpuExecutor:
-    """Device rings, per-stream workspaces and the library calls of a round."""
+    """Device rings, per-stream workspaces and the library calls of a round.
+
+    With ``config.lanes`` the device memory holds one lane per row stride:
+    read rings at that stride (a 100 bp read moves 32 bytes, not the widest
+    lane's row) and pair rings, sized by an equal share of the budget.  A
+    round's requests are grouped by lane; per lane and array the copies of
+    consecutive requests whose host and ring ranges continue each other are
+    merged, so that requests received back to back into a pinned buffer move
+    in a few large transfers."""
 
     def __init__(self, ref, config: ServeConfig, device=None):
         import torch
@@ -326,34 +386,45 @@ class GpuExecutor:
         self.torch, self.gk, self.cfg, self.ref = torch, gk, config, ref
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.dev = dev
-        self.sw = config.stride_words
-        if 32 * self.sw < config.max_read_len:
+        strides = tuple(config.lanes) if config.lanes else (config.stride_words,)
+        if max(strides) * 32 < config.max_read_len and not config.lanes:
             raise ValueError("stride_words too small for max_read_len")
         free, _ = torch.cuda.mem_get_info(dev)
         budget = int(free * config.mem_fraction)
         if config.mem_cap_bytes is not None:
             budget = min(budget, int(config.mem_cap_bytes))
         ws_bytes = max(256, gk.gk_filter_batched_workspace(config.max_round_pairs))
-        per_read = 8 * self.sw + 3
-        per_pair = 12
-        unit = per_read + per_pair * config.pairs_per_read
         rest = budget - config.n_streams * ws_bytes
-        if rest < unit * 16:
-            raise MemoryError(f"device budget {budget} B too small for the rings")
-        self.n_read_slots = int(rest // unit)
-        self.n_pair_slots = int(self.n_read_slots * config.pairs_per_read)
-        self.ring_bytes = self.n_read_slots * per_read + self.n_pair_slots * per_pair
-        e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)
-        self.packed = e(self.n_read_slots * self.sw * 2, torch.int32)
-        self.lens = e(self.n_read_slots, torch.int16)
-        self.nflag = e(self.n_read_slots, torch.uint8)
-        self.pread = e(self.n_pair_slots, torch.int32)
-        self.poff = e(self.n_pair_slots, torch.int32)
-        self.pe = e(self.n_pair_slots, torch.uint8)
-        self.acc = e(self.n_pair_slots, torch.uint8)
-        self.ed = e(self.n_pair_slots, torch.int16)
-        self.h_acc = torch.empty(self.n_pair_slots, dtype=torch.uint8, pin_memory=True)
-        self.h_ed = torch.empty(self.n_pair_slots, dtype=torch.int16, pin_memory=True)
+        share = rest // len(strides)
+        e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)  # noqa: E731
+        self.lane_bufs = []
+        self.lanes = []
+        for sw in strides:
+            per_read = 8 * sw + 3
+            per_pair = 12
+            unit = per_read + per_pair * config.pairs_per_read
+            if share < unit * 16:
+                raise MemoryError(f"device budget {budget} B too small for the rings")
+            n_reads = int(share // unit)
+            n_pairs = int(n_reads * config.pairs_per_read)
+            self.lanes.append((sw, n_reads, n_pairs))
+            self.lane_bufs.append(dict(
+                sw=sw, packed=e(n_reads * sw * 2, torch.int32), lens=e(n_reads, torch.int16),
+                nflag=e(n_reads, torch.uint8), pread=e(n_pairs, torch.int32), poff=e(n_pairs, torch.int32),
+                pe=e(n_pairs, torch.uint8), acc=e(n_pairs, torch.uint8), ed=e(n_pairs, torch.int16),
+                h_acc=torch.empty(n_pairs, dtype=torch.uint8, pin_memory=True),
+                h_ed=torch.empty(n_pairs, dtype=torch.int16, pin_memory=True)))
+            lb = self.lane_bufs[-1]
+            lb["base"] = tuple(lb[x].data_ptr() for x in ("packed", "nflag", "lens", "pread", "poff", "acc", "ed"))
+            lb["h_base"] = (lb["h_acc"].data_ptr(), lb["h_ed"].data_ptr())
+        # the single-lane view the scheduler's tests and callers read
+        self.sw = strides[0]
+        self.n_read_slots, self.n_pair_slots = self.lanes[0][1], self.lanes[0][2]
+        b0 = self.lane_bufs[0]
+        self.packed, self.lens, self.nflag = b0["packed"], b0["lens"], b0["nflag"]
+        self.pread, self.poff, self.pe, self.acc, self.ed = b0["pread"], b0["poff"], b0["pe"], b0["acc"], b0["ed"]
+        self.h_acc, self.h_ed = b0["h_acc"], b0["h_ed"]
+        self.ring_bytes = sum(nr * (8 * sw + 3) + npr * 12 for sw, nr, npr in self.lanes)
         self.streams = [torch.cuda.Stream(dev) for _ in range(config.n_streams)]
         self.ws = [e(ws_bytes, torch.uint8) for _ in range(config.n_streams)]
         self.max_req_per_round = max_req = 65536
@@ -367,6 +438,7 @@ class GpuExecutor:
                          for _ in self.streams]
         self.tiling = gk.Tiling(*config.tiling)
         self.ev0 = None
+        self.copies_last_round = 0
 
     def start(self, t0):
         self.ev0 = self.torch.cuda.Event(enable_timing=True)
@@ -376,58 +448,84 @@ class GpuExecutor:
     def launch(self, batch, slot):
         torch, gk = self.torch, self.gk
         st = self.streams[slot]
-        sw8 = self.sw * 8
         M = self.max_req_per_round
         if len(batch) > M:
             raise ValueError("too many requests in one round")
-        # pair runs contiguous in the ring, each with its per-request segments
-        runs = []  # [pair_start, n_pairs, seg_index_start, n_segs]
         hseg = self.h_seg[slot].numpy()
         hsege = self.h_sege[slot].numpy()
+        by_lane = collections.defaultdict(list)
+        for r in batch:
+            by_lane[max(r.lane, 0)].append(r)
+        plans = []  # (lane, runs): pair runs contiguous in the lane's ring, each with its segments
         dst, src, nb = [], [], []
-        for k, r in enumerate(batch):
-            dst += [self.packed.data_ptr() + r.read_slot * sw8, self.nflag.data_ptr() + r.read_slot,
-                    self.lens.data_ptr() + 2 * r.read_slot, self.pread.data_ptr() + 4 * r.pair_slot,
-                    self.poff.data_ptr() + 4 * r.pair_slot]
-            src += [r.packed.ctypes.data, r.nflag.ctypes.data, r.lens.ctypes.data, r.pair_read.ctypes.data,
-                    r.pair_off.ctypes.data]
-            nb += [r.n_reads * sw8, r.n_reads, 2 * r.n_reads, 4 * r.n_pairs, 4 * r.n_pairs]
-            if runs and runs[-1][0] + runs[-1][1] == r.pair_slot:
-                runs[-1][1] += r.n_pairs
-                runs[-1][3] += 1
-            else:
-                runs.append([r.pair_slot, r.n_pairs, k, 1])
-            hseg[k] = runs[-1][1]          # cumulative end inside its run
-            hseg[M + k] = r.read_slot      # relative ids -> ring slots
-            hsege[k] = r.e
-        n = len(batch)
+        k = 0
+        for lane, reqs in sorted(by_lane.items()):
+            b = self.lane_bufs[lane]
+            sw8 = b["sw"] * 8
+            n = len(reqs)
+            rs = np.fromiter((r.read_slot for r in reqs), np.int64, n)
+            ps = np.fromiter((r.pair_slot for r in reqs), np.int64, n)
+            nr = np.fromiter((r.n_reads for r in reqs), np.int64, n)
+            npr = np.fromiter((r.n_pairs for r in reqs), np.int64, n)
+            ptr = np.array([r.host_ptrs for r in reqs], np.int64).reshape(n, 5)
+            base = b["base"]
+            for c, (dd, nn) in enumerate(((base[0] + rs * sw8, nr * sw8), (base[1] + rs, nr),
+                                          (base[2] + 2 * rs, 2 * nr), (base[3] + 4 * ps, 4 * npr),
+                                          (base[4] + 4 * ps, 4 * npr))):
+                d, s_, z = merge_ranges(dd, ptr[:, c], nn)
+                dst.append(d)
+                src.append(s_)
+                nb.append(z)
+            # pair runs contiguous in the ring; per request the cumulative end
+            # inside its run, the id shift and the threshold
+            brk = np.ones(n, bool)
+            brk[1:] = ps[1:] != ps[:-1] + npr[:-1]
+            run_id = np.cumsum(brk) - 1
+            starts = np.flatnonzero(brk)
+            csum = np.cumsum(npr)
+            before = np.concatenate([[0], csum[:-1]])
+            hseg[k:k + n] = csum - before[starts][run_id]
+            hseg[M + k:M + k + n] = rs - np.fromiter((r.read_base for r in reqs), np.int64, n)
+            hsege[k:k + n] = np.fromiter((r.e for r in reqs), np.uint8, n)
+            ends = np.concatenate([starts[1:], [n]])
+            run_pairs = np.add.reduceat(npr, starts)
+            runs = [(int(ps[a]), int(cnt), k + int(a), int(e - a)) for a, e, cnt in zip(starts, ends, run_pairs)]
+            plans.append((lane, runs))
+            k += n
         dseg, dsege = self.d_seg[slot], self.d_sege[slot]
-        dst += [dseg.data_ptr(), dseg.data_ptr() + 8 * M, dsege.data_ptr()]
-        src += [self.h_seg[slot].data_ptr(), self.h_seg[slot].data_ptr() + 8 * M, self.h_sege[slot].data_ptr()]
-        nb += [8 * n, 8 * n, n]
-        self._copy_in(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), slot, st)
-        for p0, np_, k0, ns in runs:
-            gk.gk_rebase_pairs(self.pread[p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
-                               pair_e=self.pe[p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
-            gk.gk_filter_batched(self.ref, self.packed, self.sw, self.n_read_slots, self.lens, self.nflag,
-                                 self.pread[p0:p0 + np_], self.poff[p0:p0 + np_], self.pe[p0:p0 + np_],
-                                 self.tiling, self.ws[slot], accept=self.acc[p0:p0 + np_],
-                                 edits=self.ed[p0:p0 + np_], stream=st)
+        seg_ptr = self.h_seg[slot].data_ptr()
+        dst.append(np.array([dseg.data_ptr(), dseg.data_ptr() + 8 * M, dsege.data_ptr()], np.int64))
+        src.append(np.array([seg_ptr, seg_ptr + 8 * M, self.h_sege[slot].data_ptr()], np.int64))
+        nb.append(np.array([8 * k, 8 * k, k], np.int64))
+        dst, src, nb = (np.concatenate(x).astype(np.uint64) for x in (dst, src, nb))
+        self.copies_last_round = int(dst.shape[0])
+        self._copy_in(dst, src, nb, slot, st)
+        out_d, out_s, out_n = [], [], []
+        for lane, runs in plans:
+            b = self.lane_bufs[lane]
+            nr = self.lanes[lane][1]
+            for p0, np_, k0, ns in runs:
+                gk.gk_rebase_pairs(b["pread"][p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
+                                   pair_e=b["pe"][p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
+                gk.gk_filter_batched(self.ref, b["packed"], b["sw"], nr, b["lens"], b["nflag"],
+                                     b["pread"][p0:p0 + np_], b["poff"][p0:p0 + np_], b["pe"][p0:p0 + np_],
+                                     self.tiling, self.ws[slot], accept=b["acc"][p0:p0 + np_],
+                                     edits=b["ed"][p0:p0 + np_], stream=st)
+                out_d += [b["h_base"][0] + p0, b["h_base"][1] + 2 * p0]
+                out_s += [b["base"][5] + p0, b["base"][6] + 2 * p0]
+                out_n += [np_, 2 * np_]
         ev_dev = torch.cuda.Event(enable_timing=True)
         ev_dev.record(st)
-        dst, src, nb = [], [], []
-        for p0, np_, _, _ in runs:
-            dst += [self.h_acc.data_ptr() + p0, self.h_ed.data_ptr() + 2 * p0]
-            src += [self.acc.data_ptr() + p0, self.ed.data_ptr() + 2 * p0]
-            nb += [np_, 2 * np_]
-        gk.gk_copy_many(np.array(dst, np.uint64), np.array(src, np.uint64), np.array(nb, np.uint64), gk.D2H, st)
+        if out_n:
+            d, s_, n = merge_ranges(np.array(out_d, np.int64), np.array(out_s, np.int64), np.array(out_n, np.int64))
+            gk.gk_copy_many(d.astype(np.uint64), s_.astype(np.uint64), n.astype(np.uint64), gk.D2H, st)
         ev_host = torch.cuda.Event(enable_timing=False)
         ev_host.record(st)
         return (ev_dev, ev_host)
 
     def _copy_in(self, dst, src, nb, slot, st):
         """Host-to-device copies of a round: by default one copy-engine
-        transfer per array and request; with `gather_inputs`, one gk_gather
+        transfer per merged range; with `gather_inputs`, one gk_gather
         kernel reading the pinned request buffers (208 GB/s on this pattern
         against 135 GB/s for the copy engines on an idle GPU, but it needs
         SMs: behind the other stream's persistent filter it waits, and the
@@ -454,8 +552,9 @@ class GpuExecutor:
         return self.ev0.elapsed_time(handle[0]) * 1e-3
 
     def results(self, r: Request):
-        a = self.h_acc.numpy()[r.pair_slot:r.pair_slot + r.n_pairs].copy()
-        e = self.h_ed.numpy()[r.pair_slot:r.pair_slot + r.n_pairs].view(np.uint16).copy()
+        b = self.lane_bufs[max(r.lane, 0)]
+        a = b["h_acc"].numpy()[r.pair_slot:r.pair_slot + r.n_pairs].copy()
+        e = b["h_ed"].numpy()[r.pair_slot:r.pair_slot + r.n_pairs].view(np.uint16).copy()
         return a, e
 
 
@@ -463,25 +562,38 @@ class RequestPool:
     """Pinned host payloads that requests are cut from: per read length, reads
     sampled from the genome with their candidates (one true origin, the rest
     random), encoded once by the library's host encoder (as a client
-    sending host-encoded reads would)."""
+    sending host-encoded reads would).
+
+    stride_words: packed words per read row (None: ceil(m/32) per length,
+    the rows of a server lane of that stride).  sequential: each length's
+    requests are cut one after another from its pool (wrapping at the end),
+    as requests received back to back into a pinned buffer would lie; their
+    pair ids then number the pool's reads (read_base set accordingly) so that
+    consecutive requests' arrays continue each other.  Otherwise a request
+    starts at ``start_read`` and its ids count from its first read."""
 
     def __init__(self, ref_ascii: np.ndarray, lengths=(100, 150, 250), reads_per_len: int = 260_000,
-                 cands: int = 4, stride_words: int = 8, seed: int = 2103_14978 + 4, pin: bool = True,
-                 keep_ascii: bool = False):
+                 cands: int = 4, stride_words: int | None = 8, seed: int = 2103_14978 + 4, pin: bool = True,
+                 keep_ascii: bool = False, sequential: bool = False):
         import torch
 
         from . import gk, synth
 
-        self.sw, self.cands, self.pin = stride_words, cands, pin
+        self.cands, self.pin, self.sequential = cands, pin, sequential
+        self.sw = stride_words if stride_words is not None else 8
         self.by_len = {}
+        self.cursor = {}
         for m in lengths:
+            sw = stride_words if stride_words is not None else -(-m // 32)
             w = synth.pairs_workload(f"pool-{m}", seed=seed + m, ref=ref_ascii, n_pairs=reads_per_len * cands,
                                      m=m, cands=cands, e=0, read_edit_rate=0.02)
             packed, nflag = gk.gk_encode(torch.from_numpy(w.reads), w.n_reads, w.stride, fixed_len=m,
-                                         stride_words=stride_words)
+                                         stride_words=sw)
             self.by_len[m] = self._pin(pin, packed=packed.numpy().view(np.uint32), nflag=nflag.numpy(),
                                        lens=np.full(w.n_reads, m, np.uint16), pair_read=w.pair_read,
                                        pair_off=w.pair_off)
+            self.by_len[m]["sw"] = sw
+            self.cursor[m] = 0
             if keep_ascii:
                 self.by_len[m]["ascii"] = (None, w.reads.reshape(w.n_reads, w.stride))
         # The pool's pairs are grouped by read, `cands` per read, so the ids of
@@ -507,20 +619,36 @@ class RequestPool:
                 out[k] = (None, np.ascontiguousarray(a))
         return out
 
+    def reset(self):
+        """Restart every length's sequential cut at the pool's first read."""
+        for m in self.cursor:
+            self.cursor[m] = 0
+
     def request(self, rid: int, m: int, e: int, n_pairs: int, start_read: int, arrival: float) -> Request:
         """Cut a request of n_pairs pairs (rounded up to whole reads) of length m
-        starting at pool read `start_read`."""
+        starting at pool read `start_read` (the next read of the length's
+        pool when sequential)."""
         p = self.by_len[m]
         n_reads = -(-n_pairs // self.cands)
         total = p["lens"][1].shape[0]
-        r0 = start_read % max(1, total - n_reads)
+        if self.sequential:
+            r0 = self.cursor[m]
+            if r0 + n_reads > total:
+                r0 = 0
+            self.cursor[m] = r0 + n_reads
+        else:
+            r0 = start_read % max(1, total - n_reads)
         r1 = r0 + n_reads
         n = n_reads * self.cands
-        w2 = self.sw * 2
+        w2 = p["sw"] * 2
+        if self.sequential:  # the pool's own ids: consecutive requests' id arrays continue each other
+            ids, base = p["pair_read"][1][r0 * self.cands:r1 * self.cands], r0
+        else:
+            ids, base = self.rel_ids[1][:n], 0
         return Request(id=rid, packed=p["packed"][1][r0 * w2:r1 * w2], nflag=p["nflag"][1][r0:r1],
-                       lens=p["lens"][1][r0:r1], pair_read=self.rel_ids[1][:n],
+                       lens=p["lens"][1][r0:r1], pair_read=ids,
                        pair_off=p["pair_off"][1][r0 * self.cands:r1 * self.cands], e=e, arrival=arrival,
-                       max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None)
+                       max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None, read_base=base)
 
 
 def poisson_plan(n_requests: int, rate_per_s: float, seed: int, size_lo=1_000, size_hi=1_000_000,

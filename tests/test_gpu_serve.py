@@ -29,8 +29,29 @@ def requests(pool, n, rate, seed, size_hi=200_000):
 def oracle_of(ref, r):
     rows = np.ascontiguousarray(r.ascii).reshape(-1)
     starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, r.pair_read, r.pair_off, r.e)
+    ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
+    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, ids, r.pair_off, r.e)
     return a, e
+
+
+def test_lanes_merged_copies_equal_the_oracle(setup):
+    """Lanes per row stride (100 / 150 / 250 bp rows of 4 / 5 / 8 words),
+    requests cut back to back from their pools so that a round's copies
+    merge: every request equals the oracle, and rounds move in far fewer
+    copies than requests."""
+    ref, gkref, _ = setup
+    pool = serve.RequestPool(ref, lengths=(100, 150, 250), reads_per_len=60_000, stride_words=None,
+                             keep_ascii=True, sequential=True)
+    cfg = serve.ServeConfig(mem_cap_bytes=3 << 30, max_round_pairs=2_000_000, lanes=(4, 5, 8))
+    ex = serve.GpuExecutor(gkref, cfg)
+    reqs = requests(pool, 300, 20_000.0, 64)
+    srv = serve.Server(ex, cfg)
+    srv.run(reqs)
+    assert all(r.status == "done" for r in reqs)
+    assert max(srv.coalesced) > 10 and ex.copies_last_round < 40
+    for r in sorted(reqs, key=lambda q: q.n_pairs)[:40] + reqs[::25]:
+        a, e = oracle_of(ref, r)
+        assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits), r.id
 
 
 def test_same_result_alone_and_in_the_mix(setup):

@@ -50,9 +50,11 @@ class FakeExecutor:
     """Completes a round `delay` simulated seconds after its launch; results
     from the oracle on the request's own reads and the genome."""
 
-    def __init__(self, genome, n_read_slots, n_pair_slots, delay=0.005, never=False):
+    def __init__(self, genome, n_read_slots, n_pair_slots, delay=0.005, never=False, lanes=None):
         self.genome = genome
         self.n_read_slots, self.n_pair_slots = n_read_slots, n_pair_slots
+        if lanes:
+            self.lanes = lanes
         self.delay, self.never = delay, never
         self.now = 0.0
         self.out = {}
@@ -66,7 +68,8 @@ class FakeExecutor:
         for r in batch:
             rows = np.ascontiguousarray(r.ascii).reshape(-1)
             starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, r.pair_read, r.pair_off, r.e)
+            ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
+            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, ids, r.pair_off, r.e)
             self.out[r.id] = (a, e)
         return self.now + self.delay
 
@@ -216,3 +219,55 @@ def test_poisson_plan_for_covers_the_duration():
     arr = np.array([q["arrival"] for q in plan])
     assert arr.max() < 2.0 and arr.max() > 1.9 and (np.diff(arr) >= 0).all()
     assert 800 < len(plan) < 1200  # about 500 per second
+
+
+def test_merge_copies_joins_back_to_back_ranges():
+    d, s_, n = serve.merge_copies([100, 110, 200, 210, 300, 400], [1000, 1010, 5000, 5011, 7000, 0],
+                                  [10, 20, 10, 5, 0, 7])
+    # 100+110 continue on both sides; 210 does not continue 5000 on the source side; the empty copy drops
+    assert d.tolist() == [100, 200, 210, 400] and s_.tolist() == [1000, 5000, 5011, 0]
+    assert n.tolist() == [30, 10, 5, 7]
+
+
+def test_merge_ranges_equals_merge_copies():
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        n = int(rng.integers(0, 40))
+        nb = rng.integers(0, 5, n) * 8
+        dst = np.cumsum(np.concatenate([[1000], nb[:-1] + rng.integers(0, 2, max(n - 1, 0)) * 8]))[:n]
+        src = np.cumsum(np.concatenate([[9000], nb[:-1] + rng.integers(0, 2, max(n - 1, 0)) * 16]))[:n]
+        a = serve.merge_copies(list(dst), list(src), list(nb))
+        b = serve.merge_ranges(dst.astype(np.int64), src.astype(np.int64), nb.astype(np.int64))
+        assert all(np.array_equal(x.astype(np.int64), y) for x, y in zip(a, b))
+
+
+def test_lanes_admit_by_row_stride_and_sequential_cuts_continue():
+    """Requests go to the lane of their own row stride (60 bp: 2 words, 100
+    bp: 4), results equal the oracle; a sequential pool's consecutive
+    requests of one length continue each other in host memory."""
+    ref = synth.reference(300_000, 19, 0.05, 0.0)
+    pool = serve.RequestPool(ref, lengths=(60, 100), reads_per_len=3000, stride_words=None, pin=False,
+                             keep_ascii=True, sequential=True)
+    rng = np.random.default_rng(9)
+    reqs = [pool.request(i, int(rng.choice([60, 100])), int(rng.integers(0, 8)), int(rng.integers(4, 3000)), 0,
+                         float(rng.uniform(0, 0.01))) for i in range(40)]
+    by_m = {}
+    for r in reqs:
+        by_m.setdefault(r.max_len, []).append(r)
+    for m, rs in by_m.items():
+        assert all(r.stride_words == -(-m // 32) for r in rs)
+        for a, b in zip(rs, rs[1:]):
+            if b.read_base == a.read_base + a.n_reads:  # no wrap between them
+                assert b.packed.ctypes.data == a.packed.ctypes.data + a.packed.nbytes
+                assert b.pair_read.ctypes.data == a.pair_read.ctypes.data + a.pair_read.nbytes
+    ex = FakeExecutor(ref, 0, 0, lanes=[(2, 20_000, 80_000), (4, 20_000, 80_000)])
+    srv = serve.Server(ex, serve.ServeConfig(stride_words=4, max_read_len=128))
+    srv.run(reqs, clock=SimClock(ex), idle_sleep=0)
+    assert all(r.status == "done" for r in reqs)
+    assert {r.lane for r in by_m[60]} == {0} and {r.lane for r in by_m[100]} == {1}
+    for r in reqs[::5]:
+        rows = np.ascontiguousarray(r.ascii).reshape(-1)
+        starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
+        ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
+        a, e, _ = O.filter_batch(rows, starts, r.lens, ref, ids, r.pair_off, r.e)
+        assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits)
