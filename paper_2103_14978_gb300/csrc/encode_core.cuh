@@ -44,35 +44,55 @@ __device__ __forceinline__ void encode32(const uint32_t (&wb)[8], uint32_t nvali
   }
 }
 
-// Fast form of encode32 for reads: the planes of the first `nvalid` bytes
-// of a word and whether any of them is not A/C/G/T (either case).  Per 4
-// bytes: bit 2 (high plane) and bit 1 XOR bit 2 (low plane) of each byte
-// are gathered into 4 consecutive bits by one multiply each; validity looks
-// up the letter the byte's bits 2 and 1 name ("A", "C", "T", "G" for 00, 01,
-// 10, 11) with two byte permutes and compares it with the case-folded byte.
-// When `bad` comes back non-zero the caller re-encodes the word with
-// encode32 (codes 00 for the undefined bytes).
-__device__ __forceinline__ void encode32_fast(const uint32_t (&wb)[8], uint32_t nvalid, uint32_t &hi,
-                                              uint32_t &lo, uint32_t &bad) {
-  hi = lo = bad = 0;
+// A full word (32 bytes) -> its planes and whether any byte is not A/C/G/T
+// (either case).  Per pair of 4-byte words, bit 2
+// (high plane) and bit 1 XOR bit 2 (low plane) of each byte are gathered by
+// one multiply each into the top byte of a product, the first word's 4 bits
+// at bits 24..27 and the second's at 28..31 (the magic shifted by 4; no
+// other partial product lands in that byte, so the two products are ORed);
+// three byte permutes assemble the four top bytes into the plane word.
+// Validity looks up the letter a byte's bits 2 and 1 name ("A", "C", "T",
+// "G" for 00, 01, 10, 11) with two byte permutes and compares it with the
+// case-folded byte.  bad != 0: re-encode with encode32 (codes 00 for the
+// undefined bytes).
+__device__ __forceinline__ void encode32_full(const uint32_t (&wb)[8], uint32_t &hi, uint32_t &lo, uint32_t &bad) {
+  constexpr uint32_t kM = 0x00408102u;  // bit 2 of byte k -> bit 24 + k
+  uint32_t yh[4], yl[4];
+  bad = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t c = wb[j];
-    const uint32_t h = c & 0x04040404u;
-    const uint32_t l = (c ^ (c << 1)) & 0x04040404u;
-    // bits 2, 10, 18, 26 -> bits 24..27
-    hi |= ((h * 0x00408102u) >> 24) << (4 * j);
-    lo |= ((l * 0x00408102u) >> 24) << (4 * j);
-    const uint32_t idx = (c >> 1) & 0x03030303u;
-    const uint32_t sel = __byte_perm(idx | (idx >> 4), 0u, 0x4420u);
-    const uint32_t expect = __byte_perm(0x47544341u, 0u, sel);  // 'A' 'C' 'T' 'G'
-    const int rem = (int)nvalid - 4 * j;
-    const uint32_t keep = rem >= 4 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << (8 * rem)) - 1u));
-    bad |= ((c & 0xDFDFDFDFu) ^ expect) & keep;
+  for (int p = 0; p < 4; ++p) {
+    const uint32_t c0 = wb[2 * p], c1 = wb[2 * p + 1];
+    yh[p] = ((c0 & 0x04040404u) * kM) | ((c1 & 0x04040404u) * (kM << 4));
+    yl[p] = (((c0 ^ (c0 << 1)) & 0x04040404u) * kM) | (((c1 ^ (c1 << 1)) & 0x04040404u) * (kM << 4));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t c = wb[2 * p + q];
+      const uint32_t idx = (c >> 1) & 0x03030303u;
+      const uint32_t sel = __byte_perm(idx | (idx >> 4), 0u, 0x4420u);
+      const uint32_t expect = __byte_perm(0x47544341u, 0u, sel);  // 'A' 'C' 'T' 'G'
+      bad |= (c ^ expect) & 0xDFDFDFDFu;
+    }
   }
-  const uint32_t m = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
-  hi &= m;
-  lo &= m;
+  hi = __byte_perm(__byte_perm(yh[0], yh[1], 0x0073u), __byte_perm(yh[2], yh[3], 0x0073u), 0x5410u);
+  lo = __byte_perm(__byte_perm(yl[0], yl[1], 0x0073u), __byte_perm(yl[2], yl[3], 0x0073u), 0x5410u);
+}
+
+// Any word: the bytes past the first `nvalid` are replaced by 'A' (code 00,
+// a valid letter), so that encode32_full gives the planes of the first
+// `nvalid` bytes and flags only those.  Every lane of a warp runs the same
+// instructions whatever its word's length (the last word of a read is
+// usually short).  bad != 0: re-encode with encode32(wb, nvalid, ...).
+__device__ __forceinline__ void encode32_any(uint32_t (&wb)[8], uint32_t nvalid, uint32_t &hi, uint32_t &lo,
+                                             uint32_t &bad) {
+  if (nvalid < 32) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int rem = (int)nvalid - 4 * j;
+      const uint32_t keep = rem >= 4 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << (8 * rem)) - 1u));
+      wb[j] = (wb[j] & keep) | (0x41414141u & ~keep);
+    }
+  }
+  encode32_full(wb, hi, lo, bad);
 }
 
 }  // namespace gk

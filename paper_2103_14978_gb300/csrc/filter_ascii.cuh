@@ -32,11 +32,14 @@ __device__ __forceinline__ void load_word_bytes(const uint8_t *row, uint32_t w, 
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const uint32_t lo = 4u * k;
-    uint32_t v = 0;
+    uint32_t v = 0x41414141u;
     if (aligned && lo + 4 <= nv) {
       v = *reinterpret_cast<const uint32_t *>(b + lo);
     } else {
-      for (uint32_t i = lo; i < lo + 4 && i < nv; ++i) v |= (uint32_t)b[i] << (8 * (i - lo));
+      for (uint32_t i = lo; i < lo + 4 && i < nv; ++i) {
+        const uint32_t sh = 8 * (i - lo);
+        v = (v & ~(0xFFu << sh)) | ((uint32_t)b[i] << sh);
+      }
     }
     wb[k] = v;
   }
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocksAscii<W>::value)
       uint32_t wb[8];
       load_word_bytes(g.ascii + (uint64_t)rid * g.ascii_stride, w, nv, aligned, wb);
       uint32_t hi, lo, nb;
-      encode32_fast(wb, nv, hi, lo, nb);
+      encode32_full(wb, hi, lo, nb);
       if (nb) {
         encode32(wb, nv, hi, lo, nb);
         atomicOr(&s_undef[wib][r], 1u);

@@ -261,6 +261,27 @@ def test_device_encoder_every_byte_value_and_rare_undefined_bases():
     assert int(hn.sum()) == len(others) * len(pos)
 
 
+@pytest.mark.parametrize("stride,m,sw", [(100, 100, 4), (100, 97, 4), (64, 60, 4), (128, 128, 4), (256, 250, 8),
+                                         (32, 31, 1), (36, 33, 2), (512, 500, 16), (100, 100, 8)])
+def test_device_encoder_one_length_word_per_thread(stride, m, sw):
+    """One read length in 4-byte aligned rows with a power-of-two row (the
+    one-thread-per-word encoder): the host encoder's words and N flags, with
+    rare non-ACGT bytes, lengths not a multiple of 4 or 32 and rows wider
+    than the read (words past ceil(m/32) zero)."""
+    rng = np.random.default_rng(stride * 1000 + m)
+    valid = np.frombuffer(b"ACGTacgt", np.uint8)
+    others = np.setdiff1d(np.arange(256, dtype=np.uint8), valid)
+    n = 4099
+    asc = rng.choice(valid, n * stride)
+    hit = rng.random(n * stride) < 0.001
+    asc[hit] = rng.choice(others, int(hit.sum()))
+    hp, hn = gk.gk_encode(torch.from_numpy(asc), n, stride, fixed_len=m, stride_words=sw)
+    dp, dn = gk.gk_encode(torch.from_numpy(asc).cuda(), n, stride, fixed_len=m, stride_words=sw)
+    torch.cuda.synchronize()
+    assert torch.equal(hp, dp.cpu()) and torch.equal(hn, dn.cpu()), (stride, m, sw)
+    assert 0 < int(hn.sum()) < n
+
+
 def test_config2_structure_scaled():
     """Config 2's structure (duplicated genome regions, 4 candidates per read,
     1 true origin) at 1/500 of its size, over the whole e sweep 0..10."""
