@@ -71,18 +71,13 @@ struct PairData {
   uint2 g[W + 1]; // reference words covering the window
 };
 
-// Read words 0..W-1 and genome window words off/32 .. off/32 + W of a valid
-// pair (off + m within the genome, W = ceil(m/32) <= the row stride) in
+// Read words 0..W-1 of a valid pair (W = ceil(m/32) <= the row stride) in
 // 16-byte loads, half the requests of 8-byte loads.  With a 16-byte aligned
 // read buffer and an even row stride every read row starts on 16 bytes (an
 // odd W is below the stride, so the extra word is row padding); otherwise
-// the read takes 8-byte loads.  Window words come in aligned 16-byte loads
-// from the even word at or below off/32: ceil((W+1)/2) loads, one more when
-// W and off/32 are both odd; the last word read is at most n_words + 1,
-// inside the genome's two zero tail words.
+// the read takes 8-byte loads.
 template <int W>
-__device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t stride_words, const uint2 *ref_hl,
-                                                PairData<W> &x) {
+__device__ __forceinline__ void load_read_wide(const uint2 *reads, uint32_t stride_words, PairData<W> &x) {
   const uint2 *rp = reads + (uint64_t)x.rid * stride_words;
   if ((stride_words & 1u) == 0 && (reinterpret_cast<uintptr_t>(reads) & 15u) == 0) {
     const uint4 *rq = reinterpret_cast<const uint4 *>(rp);
@@ -96,6 +91,15 @@ __device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t str
 #pragma unroll
     for (int w = 0; w < W; ++w) x.r[w] = rp[w];
   }
+}
+
+// Genome window words off/32 .. off/32 + W of a valid pair (off + m within
+// the genome) in aligned 16-byte loads from the even word at or below
+// off/32: ceil((W+1)/2) loads, one more when W and off/32 are both odd; the
+// last word read is at most n_words + 1, inside the genome's two zero tail
+// words.
+template <int W>
+__device__ __forceinline__ void load_window_wide(const uint2 *ref_hl, PairData<W> &x) {
   constexpr int NE = (W + 2) / 2;  // ceil((W + 1) / 2)
   const uint32_t s = x.off >> 5;
   const bool odd = (s & 1u) != 0;
@@ -116,11 +120,36 @@ __device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t str
   for (int w = 0; w <= W; ++w) x.g[w] = odd ? v[w + 1] : v[w];
 }
 
+template <int W>
+__device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t stride_words, const uint2 *ref_hl,
+                                                PairData<W> &x) {
+  load_read_wide<W>(reads, stride_words, x);
+  load_window_wide<W>(ref_hl, x);
+}
+
+// Window words off/32 .. off/32 + W of a valid pair in 8-byte loads: 40
+// contiguous bytes, two 32-byte sectors.  (A copy of the genome holding
+// overlapping word pairs, read in 16-byte loads, measured 13% slower at e = 0:
+// its three loads touch three sectors.)
+template <int W, bool WIDE>
+__device__ __forceinline__ void load_window(const FilterArgs &a, PairData<W> &x) {
+  if (WIDE) {
+    load_window_wide<W>(a.ref_hl, x);
+  } else {
+    const uint2 *gp = a.ref_hl + (x.off >> 5);
+#pragma unroll
+    for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+  }
+}
+
 // Loads pair p.  WIDE: read and window words in 16-byte loads.  The plain
 // kernel keeps 8-byte loads: at e <= 2 (the launches waiting on loads) the
-// wide form measured 2-6% slower at 100 and 150 bp.
+// wide form measured 2-6% slower at 100 and 150 bp.  share (nullable): a
+// pair loaded before; when it is valid and has the same read, its read words
+// and N flag are copied instead of loaded again.
 template <int W, bool WIDE = false>
-__device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairData<W> &x) {
+__device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairData<W> &x,
+                                          const PairData<W> *share = nullptr) {
   x.rid = a.pair_read[p];
   x.off = a.pair_off[p];
   x.e = a.pair_e ? (uint32_t)a.pair_e[p] : a.fixed_e;
@@ -129,18 +158,22 @@ __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairD
   x.nflag = 0;
   x.ni = make_uint2(0, 0xffffffffu);
   if (x.status == 0 && a.m > 0) {
-    if (a.read_nflag) x.nflag = a.read_nflag[x.rid];
     if (a.ref_nidx) x.ni = a.ref_nidx[x.off >> 5];
-    if (WIDE) {
-      load_words_wide<W>(a.reads, a.stride_words, a.ref_hl, x);
+    if (share && share->status == 0 && share->rid == x.rid) {
+      x.nflag = share->nflag;
+#pragma unroll
+      for (int w = 0; w < W; ++w) x.r[w] = share->r[w];
     } else {
-      const uint2 *rp = a.reads + (uint64_t)x.rid * a.stride_words;
-      const uint2 *gp = a.ref_hl + (x.off >> 5);
+      if (a.read_nflag) x.nflag = a.read_nflag[x.rid];
+      if (WIDE) {
+        load_read_wide<W>(a.reads, a.stride_words, x);
+      } else {
+        const uint2 *rp = a.reads + (uint64_t)x.rid * a.stride_words;
 #pragma unroll
-      for (int w = 0; w < W; ++w) x.r[w] = rp[w];
-#pragma unroll
-      for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+        for (int w = 0; w < W; ++w) x.r[w] = rp[w];
+      }
     }
+    load_window<W, WIDE>(a, x);
   }
 }
 
@@ -697,7 +730,8 @@ __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p
   if constexpr (VARIANT == 3) {
     sweep_and_write<W>(a, p, x);
   } else {
-    const uint32_t count = VARIANT == 2 ? filter_loaded_deferred<W>(a, x) : filter_loaded<W, VARIANT == 1>(a, x);
+    const uint32_t count = VARIANT == 2 || VARIANT == 4 ? filter_loaded_deferred<W>(a, x)
+                                                        : filter_loaded<W, VARIANT == 1>(a, x);
     write_count(a, p, count, x.e);
   }
 }
@@ -923,27 +957,36 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
   }
 }
 
-// Resident blocks per SM of the two-pairs-per-thread kernel.
+// The two-pairs-per-thread kernel gathers in 8-byte loads: 16-byte loads
+// (load_words_wide) measured 4% slower at e = 0 and 1, 100 bp.
+constexpr bool kPair2Wide = false;
+
+// Resident blocks per SM of the two-pairs-per-thread kernel: 4 (64 registers,
+// a few spilled) measured faster than 3 (80 registers, no spill) at every
+// threshold 1..10 and in the 0..10 sweep at 100 bp on GB300 (e = 2: 53.3 ->
+// 57.5 Gpairs/s; the sweep 1.307 -> 1.280 ms), the same at e = 0.
 template <int W>
 struct MinBlocks2 {
-  static constexpr int value = W <= 2 ? 4 : 3;
+  static constexpr int value = 4;
 };
 
 // Deferred erosion (VARIANT 2, or the sweep, VARIANT 3), two pairs per
 // thread: pairs 2t and 2t+1.  When both are filtered and share their read
-// (the candidates of one read usually sit next to each other), the read's
-// shifted copies serve both windows: a shift step costs about 13W integer
-// operations per pair instead of 15W.  Otherwise each pair is filtered on its
-// own.
-template <int W, int VARIANT>
+// (the candidates of one read usually sit next to each other), the read is
+// loaded once and its shifted copies serve both windows: a shift step costs
+// about 13W integer operations per pair instead of 15W.  Otherwise each pair
+// is filtered on its own.  VARIANT 4: one threshold whose shift count KC
+// (0..2, below m) is a compile-time constant, so the shift steps unroll and
+// the end corrections of K = 0 vanish.
+template <int W, int VARIANT, int KC = -1>
 __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_pair2_kernel(const FilterArgs a) {
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t p0 = 2 * t, p1 = p0 + 1;
   const bool act0 = p0 < a.n_pairs, act1 = p1 < a.n_pairs;
   PairData<W> x0, x1;
   x0.status = x1.status = 0;
-  if (act0) load_pair<W>(a, p0, x0);
-  if (act1) load_pair<W>(a, p1, x1);
+  if (act0) load_pair<W, kPair2Wide>(a, p0, x0);
+  if (act1) load_pair<W, kPair2Wide>(a, p1, x1, act0 ? &x0 : nullptr);
   if (a.err_count) {
     const unsigned b0 = __ballot_sync(0xffffffffu, act0 && x0.status == 2);
     const unsigned b1 = __ballot_sync(0xffffffffu, act1 && x1.status == 2);
@@ -997,7 +1040,8 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
                                     }
                                   });
     } else {
-      deferred_counts<W, 2>(a, a.m, min(a.fixed_e, a.m - 1), rh, rl, gh, gl, count);
+      const uint32_t K = KC >= 0 ? (uint32_t)KC : min(a.fixed_e, a.m - 1);
+      deferred_counts<W, 2>(a, a.m, K, rh, rl, gh, gl, count);
       write_count(a, p0, count[0], a.fixed_e);
       write_count(a, p1, count[1], a.fixed_e);
     }
@@ -1012,19 +1056,36 @@ template <int W, int VARIANT>
 cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
   unsigned blocks = (unsigned)((a.n_pairs + kFilterThreads - 1) / kFilterThreads);
   if (a.compact == 0) {
-    // Two pairs per thread only while it keeps 3 blocks per SM (W <= 4): at
-    // W = 5 (2 blocks) it measured 40% slower at e = 2, 150 bp.
-    if constexpr ((VARIANT == 2 || VARIANT == 3) && W <= 4) {
+    // Two pairs per thread for W <= 4 only: at W = 5 (2 blocks per SM with
+    // its registers unspilled) it measured 40% slower at e = 2, 150 bp.
+    if constexpr ((VARIANT == 2 || VARIANT == 3 || VARIANT == 4) && W <= 4) {
       if (a.m > 0) {
         const uint64_t threads = (a.n_pairs + 1) / 2;
-        filter_pair2_kernel<W, VARIANT><<<(unsigned)((threads + kFilterThreads - 1) / kFilterThreads), kFilterThreads, 0,
-                                 stream>>>(a);
+        const unsigned grid = (unsigned)((threads + kFilterThreads - 1) / kFilterThreads);
+        if constexpr (VARIANT == 4) {
+          // shift count = the threshold, 0..2, below m (checked by the caller)
+          switch (a.fixed_e) {
+            case 0: filter_pair2_kernel<W, 4, 0><<<grid, kFilterThreads, 0, stream>>>(a); break;
+            case 1: filter_pair2_kernel<W, 4, 1><<<grid, kFilterThreads, 0, stream>>>(a); break;
+            case 2: filter_pair2_kernel<W, 4, 2><<<grid, kFilterThreads, 0, stream>>>(a); break;
+            default: return cudaErrorInvalidValue;
+          }
+        } else {
+          filter_pair2_kernel<W, VARIANT><<<grid, kFilterThreads, 0, stream>>>(a);
+        }
         return cudaGetLastError();
       }
     }
-    filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
-    return cudaGetLastError();
+    if constexpr (VARIANT == 4) {
+      return cudaErrorInvalidValue;  // VARIANT 4 is the two-pair kernel only
+    } else {
+      filter_kernel<W, VARIANT, false><<<blocks, kFilterThreads, 0, stream>>>(a);
+      return cudaGetLastError();
+    }
   }
+  if constexpr (VARIANT == 4) {
+    return cudaErrorInvalidValue;
+  } else {
   // Persistent warps: a few waves of resident blocks.  The dynamic shared
   // memory limit and the occupancy are set up once per device (threads that
   // race here repeat the same idempotent setup; the block count is
@@ -1055,6 +1116,7 @@ cudaError_t launch_filter_variant(const FilterArgs &a, cudaStream_t stream) {
   if (blocks > wave) blocks = (unsigned)wave;
   filter_kernel<W, VARIANT, true><<<blocks, kFilterThreads, smem, stream>>>(a);
   return cudaGetLastError();
+  }
 }
 
 }  // namespace gk

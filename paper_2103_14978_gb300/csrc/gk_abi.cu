@@ -39,8 +39,13 @@ int cuda_check(cudaError_t err, const char *what) {
 
 // Variant of the per-pair code for a launch: 2 deferred erosion, 1 exact
 // with every shift below 32, 0 exact for any thresholds.
-int filter_variant(const FilterArgs &a) {
+int filter_variant(const FilterArgs &a, bool pair_k) {
   if (a.out_stride != 0) return 3;  // a threshold sweep (gk_filter_sweep)
+  // One threshold 0..2 below m, reads of at most 128 bases, no compaction:
+  // the two-pairs-per-thread deferred kernel with the shift count fixed at
+  // compile time (measured on GB300 at 100 bp against the exact one-pair
+  // kernel at e = 0, 1 and the runtime-K form at e = 2).
+  if (pair_k && a.edge_on && !a.pair_e && a.fixed_e <= 2 && a.m > a.fixed_e && a.m <= 128 && !a.compact) return 4;
   // Every shift count below 32 (one threshold under 32, or reads of at most
   // 32 bases): the edge vectors live in the end words only.
   const bool small = (!a.pair_e && a.fixed_e < 32) || a.m <= 32;
@@ -52,7 +57,7 @@ int filter_variant(const FilterArgs &a) {
 }
 
 cudaError_t launch_filter(int W, const FilterArgs &a, cudaStream_t stream) {
-  const int variant = filter_variant(a);
+  const int variant = filter_variant(a, true);
   if (W >= 1 && W <= 4) return launch_filter_w1_4(W, variant, a, stream);
   if (W <= 8) return launch_filter_w5_8(W, variant, a, stream);
   if (W <= 12) return launch_filter_w9_12(W, variant, a, stream);
@@ -375,7 +380,7 @@ int gk_filter_ascii(gk_ref_t ref, const uint8_t *ascii, uint64_t ascii_stride, u
   g.ascii_stride = ascii_stride;
   g.rows_aligned = (aligned(ascii, 4) && ascii_stride % 4 == 0) ? 1 : 0;
   const int W = m == 0 ? 1 : (int)((m + 31) / 32);
-  const int variant = gk::filter_variant(a);
+  const int variant = gk::filter_variant(a, false);
   const cudaError_t err = W <= 8 ? gk::launch_filter_ascii_w1_8(W, variant, g, (cudaStream_t)stream)
                                  : gk::launch_filter_ascii_w9_16(W, variant, g, (cudaStream_t)stream);
   return gk::cuda_check(err, "gk_filter_ascii: launch");
