@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="config 2 only (no config 3/4/5 keys)")
     ap.add_argument("--level-seconds", type=float, default=10.0, help="arrival time per serving load level")
     ap.add_argument("--round-pairs", type=int, default=32_000_000, help="pairs per serving round, at most")
+    ap.add_argument("--serve-streams", type=int, default=3, help="streams of the serving executor")
     return ap.parse_args()
 
 
@@ -535,12 +536,21 @@ def run_mine(args):
         tops = ops / (sum(per_e_ms) * 1e-3) / 1e12
         bpp = bytes_per_pair(m, c, False)
         gbs = w.n_pairs * bpp * len(E_SWEEP) / (sum(per_e_ms) * 1e-3) / 1e9
+        # Per threshold: the launch against the slower of its bytes at the
+        # HBM peak and its word-formulation ops at the integer peak.
+        per_e = {}
+        for e, ms in zip(E_SWEEP, per_e_ms):
+            ceil = min(hbm_peak * 1e9 / bpp, ALU_PEAK_TOPS * 1e12 / ops_per_pair(m, e))
+            rate = w.n_pairs / (ms * 1e-3)
+            per_e[str(e)] = {"gpairs_s": rate / 1e9, "roofline_gpairs_s": ceil / 1e9, "frac": rate / ceil}
         return {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                 "frac": tops / ALU_PEAK_TOPS, "traffic": recorded_traffic("c2-100bp-e0..10"),
-                "kernel": "filter_kernel<4, 1, 0> (e 0-1) | filter_pair2_kernel<4> (e 2-10)",
+                "kernel": ("filter_pair2_kernel<W, 4, K> (e 0-2, two pairs per thread, shift count fixed at "
+                           "compile time) | filter_pair2_kernel<W, 2> (e 3-10)"),
                 "ops_basis": "W*(9 + 22e + 4) per pair (word formulation)", "peak_basis": peak_basis,
                 "bytes_side": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
-                               "bytes_per_pair": bpp}}
+                               "bytes_per_pair": bpp},
+                "per_e_of_roofline": per_e}
 
     def sliced_roofline(per_e_ms, slice_ms):
         """Bit-sliced formulation: its algorithmic ops and bytes per launch,
@@ -1084,7 +1094,8 @@ def measure_c5(args) -> dict:
     # Requests arrive back to back in per-length pinned buffers (sequential
     # cuts, rows at each length's own stride); the server has one lane per
     # stride.
-    pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000, stride_words=None, sequential=True)
+    pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000, stride_words=None, sequential=True,
+                             pair_format="starts")
     lanes = tuple(sorted({pool.by_len[m]["sw"] for m in lengths}))
     stream = torch.cuda.current_stream()
     per_combo = {}  # the plain filter on the mix, every (m, e) equally likely
@@ -1104,7 +1115,12 @@ def measure_c5(args) -> dict:
     plain = 1.0 / np.mean([1.0 / v for v in per_combo.values()])
     lo, hi = 1_000, 1_000_000
     mean_size = (hi - lo) / np.log(hi / lo)
-    cfg = serve.ServeConfig(mem_cap_bytes=16 << 30, max_round_pairs=args.round_pairs, copy_results=False, lanes=lanes)
+    # Candidates as one start per read (expanded on the device), results as
+    # one byte per pair, three streams: the host link carries about 17 bytes
+    # per pair in and 1 out, and a round's copies run while the previous
+    # round filters.
+    cfg = serve.ServeConfig(mem_cap_bytes=16 << 30, max_round_pairs=args.round_pairs, copy_results=False, lanes=lanes,
+                            pair_format="starts", result_bytes=True, n_streams=args.serve_streams)
     ex = serve.GpuExecutor(gkref, cfg)
     skip = 1.0
 
@@ -1126,6 +1142,7 @@ def measure_c5(args) -> dict:
     for load in (0.5, 0.8, 0.95):
         levels[str(load)] = level(load * capacity, args.level_seconds, 2103_14978 + 5 + int(load * 100))
         levels[str(load)]["load"] = load
+    h2d_pp = float(np.mean([(8 * pool.by_len[m]["sw"] + 2 + 1 + 4) / pool.cands + 4 for m in lengths]))
     ok = all(abs(v["served_gpairs_s"] / v["offered_gpairs_s"] - 1) < 0.05 for v in levels.values())
     mono = levels["0.5"]["p99_ms"] <= levels["0.8"]["p99_ms"] <= levels["0.95"]["p99_ms"]
     gkref.close()
@@ -1139,8 +1156,14 @@ def measure_c5(args) -> dict:
                       f"latency = arrival -> results on the host, over requests arriving after {skip:g} s",
             "lanes": [{"row_words": sw, "read_slots": nr, "pair_slots": npr} for sw, nr, npr in ex.lanes],
             "copies_per_round_last": ex.copies_last_round,
+            "streams": cfg.n_streams,
+            "host_link_bytes_per_pair": {"in": h2d_pp, "out": 1.0,
+                                         "basis": "per read: packed row (8 x row words) + length 2 + N flag 1 + "
+                                                  "start 4, per pair: offset 4; 4 candidates per read, lengths "
+                                                  "100/150/250 equally likely"},
             "inputs": "requests received back to back into per-length pinned buffers (rows at each length's "
-                      "own stride); a round's copies merge per lane and array"}
+                      "own stride); a round's copies merge per lane and array; candidates as one start per read "
+                      "(gk_expand_pairs), results as one byte per pair (GK_FLAG_RESULT_BYTE)"}
 
 
 def run_config(args, which: str):

@@ -324,6 +324,10 @@ uint64_t gk_filter_batched_workspace(uint64_t n_pairs);
  *   read_len    device, n_reads uint16 lengths (each read may differ; a read
  *               longer than GK_MAX_LEN or than 32*stride_words makes its
  *               pairs invalid)
+ *   flags       GK_FLAG_RESULT_BYTE is allowed with pair_e: accept_out gets
+ *               the result bytes (edits_out may be NULL); a pair's decision
+ *               reads from its byte only for thresholds <= 252, which the
+ *               caller keeps (the bytes themselves are defined for any e)
  *   tiling      host pointer, see gk_tiling_t
  *   workspace   device scratch of at least gk_filter_batched_workspace(
  *               n_pairs) bytes, 256-byte aligned, owned by the caller; its
@@ -362,6 +366,39 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
 int gk_rebase_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs,
                     const uint64_t *seg_end, const int64_t *seg_delta,
                     const uint8_t *seg_e, uint32_t n_segs, void *stream);
+
+/*
+ * gk_expand_pairs -- per-pair read ids and thresholds of a coalesced launch
+ * from per-read start offsets, so that a request's candidates travel as
+ * their offsets plus one 32-bit start per read (CSR rows: read k's
+ * candidates are pairs start[k] .. start[k+1]-1 of its request) instead of
+ * one read id per pair (the paper's batches hold each read with its
+ * candidate locations, Sec. 3.5).
+ *
+ * The launch covers pairs [0, n_pairs) of pair_read / pair_e and n_reads
+ * reads numbered across n_segs segments (requests):
+ *   seg_read_end   device, n_segs uint64: cumulative read counts (segment i
+ *                  owns reads [seg_read_end[i-1], seg_read_end[i]))
+ *   seg_pair_end   device, n_segs uint64: cumulative pair counts (segment i
+ *                  owns pairs [seg_pair_end[i-1], seg_pair_end[i]))
+ *   seg_read_slot  device, n_segs uint64: the read-buffer row of segment i's
+ *                  first read (its reads occupy consecutive rows)
+ *   seg_start_base device, n_segs uint32: subtracted (mod 2^32) from segment
+ *                  i's start values, so that a request cut from a larger
+ *                  numbering needs no rewriting
+ *   seg_e          device, n_segs uint8 thresholds
+ *   read_start     device, uint32 per read-buffer row: the start value of the
+ *                  read in that row
+ * Writes pair_read[j] = the row of the read owning pair j and pair_e[j] =
+ * its segment's threshold.  Starts are clamped to the segment's pairs; a
+ * pair that no read claims (starts decreasing or skipping pairs) gets id
+ * 0xFFFFFFFF, which the filters report as an invalid pair.  Asynchronous on
+ * `stream`.
+ */
+int gk_expand_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint32_t *read_start,
+                    const uint64_t *seg_read_end, const uint64_t *seg_pair_end, const uint64_t *seg_read_slot,
+                    const uint32_t *seg_start_base, const uint8_t *seg_e, uint32_t n_segs, uint64_t n_reads,
+                    void *stream);
 
 /*
  * gk_copy_many -- n asynchronous copies on `stream`, one cudaMemcpyAsync

@@ -78,8 +78,7 @@ __global__ void __launch_bounds__(kPlanThreads) classify_kernel(const BatchArgs 
         key = key_of(W, min(K, 255u));
         atomicAdd(&hist[key], 1u);
       } else {
-        a.f.accept[p] = status != 2;
-        a.f.edits[p] = status == 2 ? GK_EDITS_INVALID : (status == 1 ? GK_EDITS_UNDEFINED : 0);
+        write_trivial(a.f, p, status == 3 ? 0 : status);  // an empty read: count 0, accepted
       }
       a.s.km[p] = key | (mm << 16);
     }

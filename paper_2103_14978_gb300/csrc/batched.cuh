@@ -80,8 +80,7 @@ __device__ __forceinline__ void tile_whole(const BatchArgs &a, uint32_t first, u
       load_words_wide<W>(a.f.reads, a.f.stride_words, a.f.ref_hl, x);
       const uint32_t count = deferred ? filter_loaded_deferred<W>(a.f, x)
                                       : (K < 32 ? filter_loaded<W, true>(a.f, x) : filter_loaded<W, false>(a.f, x));
-      a.f.accept[rec.x] = count <= x.e;
-      a.f.edits[rec.x] = (uint16_t)count;
+      write_count(a.f, rec.x, count, x.e);
     }
   }
 }
@@ -215,8 +214,7 @@ __device__ __forceinline__ void tile_coop(const BatchArgs &a, uint32_t first, ui
       }
       const uint32_t count = coop_filter<WPT>(rh, rl, gh, gl, vm, K, edge_on, a.f.count_mode, g);
       if (valid && g.lig == 0) {
-        a.f.accept[p] = count <= e;
-        a.f.edits[p] = (uint16_t)count;
+        write_count(a.f, p, count, e);
       }
     }
   }

@@ -398,7 +398,8 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
   if (!ref) return fail(GK_EINVAL, "gk_filter_batched: null reference handle");
   if (n_pairs == 0) return GK_OK;
   if (n_pairs >= (1ull << 32)) return fail(GK_ERANGE, "gk_filter_batched: n_pairs must be < 2^32");
-  if (!reads || !read_len || !pair_read || !pair_off || !accept_out || !edits_out || !tiling)
+  const bool result_byte = (flags & GK_FLAG_RESULT_BYTE) != 0;
+  if (!reads || !read_len || !pair_read || !pair_off || !accept_out || (!edits_out && !result_byte) || !tiling)
     return fail(GK_EINVAL, "gk_filter_batched: null buffer");
   if (stride_words == 0 || stride_words > GK_MAX_LEN / 32)
     return fail(GK_EINVAL, "gk_filter_batched: stride_words must be 1..GK_MAX_LEN/32");
@@ -406,7 +407,7 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
   if (!pair_e && fixed_e > 255) return fail(GK_ERANGE, "gk_filter_batched: fixed_e above 255");
   if (count_mode != GK_COUNT_RUNS4 && count_mode != GK_COUNT_POPCOUNT)
     return fail(GK_EINVAL, "gk_filter_batched: unknown count_mode");
-  if (flags & ~GK_FLAG_NO_EDGE_FIX) return fail(GK_EINVAL, "gk_filter_batched: unknown flags");
+  if (flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE)) return fail(GK_EINVAL, "gk_filter_batched: unknown flags");
   const gk_tiling_t t = *tiling;
   if (!(t.words_per_thread == 1 || t.words_per_thread == 2 || t.words_per_thread == 3 ||
         t.words_per_thread == 4 || t.words_per_thread == 6 || t.words_per_thread == 8))
@@ -434,6 +435,7 @@ int gk_filter_batched(gk_ref_t ref, const uint32_t *reads, uint32_t stride_words
   a.f.edge_on = (flags & GK_FLAG_NO_EDGE_FIX) ? 0 : 1;
   a.f.accept = accept_out;
   a.f.edits = edits_out;
+  a.f.result_byte = result_byte ? 1 : 0;
   a.f.err_count = err_count;
   a.read_len = read_len;
   a.tile_pairs = t.tile_pairs;

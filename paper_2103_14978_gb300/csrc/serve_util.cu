@@ -26,7 +26,59 @@ __global__ void rebase_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restr
   if (pair_e) pair_e[p] = seg_e[lo];
 }
 
+// One thread per read of the launch (reads numbered across the segments):
+// its segment by binary search, its slot, its pairs from the start offsets,
+// clamped to the segment's pairs.
+__global__ void expand_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restrict__ pair_e,
+                              const uint32_t *__restrict__ read_start, const uint64_t *__restrict__ seg_read_end,
+                              const uint64_t *__restrict__ seg_pair_end, const uint64_t *__restrict__ seg_read_slot,
+                              const uint32_t *__restrict__ seg_start_base, const uint8_t *__restrict__ seg_e,
+                              uint32_t n_segs, uint64_t n_vreads, uint64_t n_pairs) {
+  const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (v >= n_vreads) return;
+  uint32_t lo = 0, hi = n_segs - 1;  // first segment whose read end exceeds v
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (seg_read_end[mid] > v) hi = mid; else lo = mid + 1;
+  }
+  const uint64_t r0 = lo ? seg_read_end[lo - 1] : 0, p0 = lo ? seg_pair_end[lo - 1] : 0;
+  const uint64_t np = seg_pair_end[lo] - p0;
+  const uint64_t slot = seg_read_slot[lo] + (v - r0);
+  const uint32_t base = seg_start_base[lo];
+  const uint64_t a = (uint32_t)(read_start[slot] - base);
+  const uint64_t b = v + 1 < seg_read_end[lo] ? (uint64_t)(uint32_t)(read_start[slot + 1] - base) : np;
+  const uint64_t from = a < np ? a : np, to = b < np ? b : np;
+  const uint32_t id = slot <= 0xFFFFFFFEull ? (uint32_t)slot : 0xFFFFFFFFu;
+  const uint8_t e = seg_e[lo];
+  const uint64_t end = p0 + to < n_pairs ? p0 + to : n_pairs;  // never past the launch's pairs
+  for (uint64_t j = p0 + from; j < end; ++j) {
+    pair_read[j] = id;
+    pair_e[j] = e;
+  }
+}
+
 }  // namespace
+
+extern "C" int gk_expand_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint32_t *read_start,
+                               const uint64_t *seg_read_end, const uint64_t *seg_pair_end,
+                               const uint64_t *seg_read_slot, const uint32_t *seg_start_base,
+                               const uint8_t *seg_e, uint32_t n_segs, uint64_t n_reads, void *stream) {
+  gk::clear_error();
+  if (n_pairs == 0) return GK_OK;
+  if (!pair_read || !pair_e || !read_start || !seg_read_end || !seg_pair_end || !seg_read_slot ||
+      !seg_start_base || !seg_e || n_segs == 0)
+    return gk::fail(GK_EINVAL, "gk_expand_pairs: null buffer or no segments");
+  cudaStream_t st = (cudaStream_t)stream;
+  // Pairs that no read claims stay invalid (an id no read has).
+  cudaError_t err = cudaMemsetAsync(pair_read, 0xFF, n_pairs * sizeof(uint32_t), st);
+  if (err != cudaSuccess) return gk::cuda_check(err, "gk_expand_pairs: fill");
+  if (n_reads == 0) return GK_OK;
+  const int threads = 256;
+  expand_kernel<<<(unsigned)((n_reads + threads - 1) / threads), threads, 0, st>>>(
+      pair_read, pair_e, read_start, seg_read_end, seg_pair_end, seg_read_slot, seg_start_base, seg_e, n_segs,
+      n_reads, n_pairs);
+  return gk::cuda_check(cudaGetLastError(), "gk_expand_pairs: launch");
+}
 
 extern "C" int gk_rebase_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint64_t *seg_end,
                                const int64_t *seg_delta, const uint8_t *seg_e, uint32_t n_segs, void *stream) {

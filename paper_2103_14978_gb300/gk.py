@@ -76,6 +76,8 @@ _SIGS = {
                                    _c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
     "gk_rebase_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                          _c.c_uint32, _c.c_void_p], _c.c_int),
+    "gk_expand_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                         _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p], _c.c_int),
     "gk_copy_many": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_int, _c.c_void_p], _c.c_int),
     "gk_gather": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_pipe_create": ([_c.c_void_p, _c.POINTER(PipeDesc), _c.POINTER(_c.c_void_p)], _c.c_int),
@@ -420,12 +422,13 @@ def gk_filter_batched(ref: Reference, reads: torch.Tensor, stride_words: int, n_
     """Filter pairs of mixed read lengths in one persistent launch
     (gk_filter_batched).  ``read_len`` is an int16 CUDA tensor (uint16
     values); ``workspace`` a uint8 CUDA tensor of at least
-    gk_filter_batched_workspace(n) bytes.  Returns (accept, edits)."""
+    gk_filter_batched_workspace(n) bytes.  Returns (accept, edits); with
+    GK_FLAG_RESULT_BYTE, (result bytes, None) unless ``edits`` is given."""
     n = pair_read.numel()
     dev = pair_read.device
     if accept is None:
         accept = torch.empty(n, dtype=torch.uint8, device=dev)
-    if edits is None:
+    if edits is None and not flags & GK_FLAG_RESULT_BYTE:
         edits = torch.empty(n, dtype=torch.int16, device=dev)
     if reads.numel() < n_reads * stride_words * 2:
         raise ValueError("reads holds fewer than n_reads * stride_words * 2 words")
@@ -460,6 +463,28 @@ def gk_filter_batched_noalloc(ref: Reference, reads: torch.Tensor, stride_words:
         count_mode, flags, ctypes.byref(tiling), _dptr(accept, torch.uint8, "accept", n),
         _dptr(edits, torch.int16, "edits", n), _dptr(err_count, torch.int32, "err_count", 1), _stream(stream)))
     return accept, edits
+
+
+def gk_expand_pairs(pair_read: torch.Tensor, pair_e: torch.Tensor, read_start: torch.Tensor,
+                    seg_read_end: torch.Tensor, seg_pair_end: torch.Tensor, seg_read_slot: torch.Tensor,
+                    seg_start_base: torch.Tensor, seg_e: torch.Tensor, n_reads: int | None = None, stream=None):
+    """Per-pair read ids (read-buffer rows) and thresholds of the pairs of
+    n_segs requests from their reads' start offsets (gk_expand_pairs):
+    segment i owns reads [seg_read_end[i-1], seg_read_end[i]) at rows
+    seg_read_slot[i] + k and pairs [seg_pair_end[i-1], seg_pair_end[i]);
+    read_start[row] - seg_start_base[i] is the read's first pair within its
+    request.  int64 / int32 / uint8 CUDA tensors as in gk.h."""
+    n_segs = seg_read_end.numel()
+    n = pair_read.numel()
+    if n_reads is None:
+        n_reads = int(seg_read_end[-1].item()) if n_segs else 0
+    _check(lib().gk_expand_pairs(_dptr(pair_read, torch.int32, "pair_read"), _dptr(pair_e, torch.uint8, "pair_e", n),
+                                 n, _dptr(read_start, torch.int32, "read_start"),
+                                 _dptr(seg_read_end, torch.int64, "seg_read_end"),
+                                 _dptr(seg_pair_end, torch.int64, "seg_pair_end", n_segs),
+                                 _dptr(seg_read_slot, torch.int64, "seg_read_slot", n_segs),
+                                 _dptr(seg_start_base, torch.int32, "seg_start_base", n_segs),
+                                 _dptr(seg_e, torch.uint8, "seg_e", n_segs), n_segs, n_reads, _stream(stream)))
 
 
 def gk_rebase_pairs(pair_read: torch.Tensor, seg_end: torch.Tensor, seg_delta: torch.Tensor,

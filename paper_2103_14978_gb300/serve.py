@@ -12,7 +12,11 @@ rejected.
 
 Requests arrive host-encoded (2-bit planes written by gk_encode's host path,
 the paper's host-encoded mode, Sec. 3.3): a 100 bp read moves as 32 bytes
-instead of 100.
+instead of 100.  A request's candidates come as one read id per pair, or
+(pair_format "starts") as each read's first-candidate index, CSR style: one
+32-bit value per read instead of one per pair, expanded on the device by
+gk_expand_pairs.  With result_bytes the results return as one byte per pair
+(GK_FLAG_RESULT_BYTE) instead of an accept byte and a 16-bit count.
 
 Rounds.  Whenever a stream is free, every admitted request not yet launched
 (up to `max_round_pairs` pairs) forms one round: one gk_copy_many call moves
@@ -40,17 +44,21 @@ GK_MAX_WORDS = 16
 class Request:
     """One request: ``packed`` uint32 reads as gk_encode writes them
     (n_reads x stride_words x 2, the stride of one of the server's lanes),
-    ``nflag`` uint8 and ``lens`` uint16 per read, ``pair_read`` uint32 read
-    ids (id - ``read_base`` indexes these reads), ``pair_off`` uint32 genome
-    offsets, one threshold ``e``.  For asynchronous copies the arrays should
-    live in pinned host memory.  ``arrival`` is the time (s, from the start
-    of ``run``) the request arrives."""
+    ``nflag`` uint8 and ``lens`` uint16 per read, ``pair_off`` uint32 genome
+    offsets, one threshold ``e``, and the pairs' reads as either
+    ``pair_read`` uint32 read ids (id - ``read_base`` indexes these reads) or
+    ``read_start`` uint32 per read (pairs read_start[k] - start_base ..
+    read_start[k+1] - start_base - 1 are read k's; the last read's run ends
+    at the last pair).  For asynchronous copies the arrays should live in
+    pinned host memory.  ``arrival`` is the time (s, from the start of
+    ``run``) the request arrives.  Results: ``accept`` and ``edits``, or with
+    a result-byte server the result bytes in ``accept`` and ``edits`` None."""
 
     id: int
     packed: np.ndarray
     nflag: np.ndarray
     lens: np.ndarray
-    pair_read: np.ndarray
+    pair_read: np.ndarray | None
     pair_off: np.ndarray
     e: int
     arrival: float = 0.0
@@ -68,16 +76,27 @@ class Request:
     ascii: np.ndarray | None = None  # the reads' ASCII rows, kept only for checking
     read_base: int = 0  # pair_read - read_base indexes these reads (ids of a larger numbering)
     lane: int = -1
+    read_start: np.ndarray | None = None  # CSR form of the pairs' reads (instead of pair_read)
+    start_base: int = 0                   # read_start - start_base counts from this request's first pair
 
     def __post_init__(self):
         # Sizes and host addresses are read once here: the scheduler handles
         # tens of thousands of requests a second.  n_reads, n_pairs and
-        # stride_words (packed words per read row) are plain attributes.
+        # stride_words (packed words per read row) are plain attributes;
+        # host_ptrs[3] is the pair-to-read array of either form.
+        if (self.pair_read is None) == (self.read_start is None):
+            raise ValueError("a request gives exactly one of pair_read and read_start")
         self.n_reads = int(self.lens.shape[0])
-        self.n_pairs = int(self.pair_read.shape[0])
+        self.n_pairs = int(self.pair_off.shape[0])
+        if self.pair_read is not None and self.pair_read.shape[0] != self.n_pairs:
+            raise ValueError("pair_read and pair_off differ in length")
+        if self.read_start is not None and self.read_start.shape[0] != self.n_reads:
+            raise ValueError("read_start needs one value per read")
+        self.pair_format = "ids" if self.pair_read is not None else "starts"
         self.stride_words = int(self.packed.size // (2 * self.n_reads)) if self.n_reads else 0
+        link = self.pair_read if self.pair_read is not None else self.read_start
         self.host_ptrs = tuple(int(x.__array_interface__["data"][0])
-                               for x in (self.packed, self.nflag, self.lens, self.pair_read, self.pair_off))
+                               for x in (self.packed, self.nflag, self.lens, link, self.pair_off))
 
     def cancel(self) -> bool:
         """Cancel a request that has not been admitted yet."""
@@ -172,6 +191,8 @@ class ServeConfig:
     gather_inputs: bool = False       # move a round's inputs with one gk_gather kernel instead of
                                       # one copy-engine transfer per array and request
     gather_entries: int = 1 << 17     # gather table capacity per stream (64 KiB entries)
+    pair_format: str = "ids"          # requests' pair-to-read form: "ids" or "starts" (CSR)
+    result_bytes: bool = False        # results as one byte per pair (thresholds <= 252)
 
 
 @dataclasses.dataclass
@@ -213,7 +234,8 @@ class Server:
                 and r.n_pairs <= self.cfg.max_round_pairs
                 and (r.max_len if r.max_len >= 0 else int(r.lens.max(initial=0))) <= min(
                     self.cfg.max_read_len, 32 * self.lane_stride[lane])
-                and 0 <= r.e <= 255)
+                and 0 <= r.e <= (252 if self.cfg.result_bytes else 255)
+                and getattr(r, "pair_format", "ids") == self.cfg.pair_format)
 
     def _admit(self, r: Request, now: float) -> bool:
         lane = self.lane_of(r)
@@ -399,9 +421,12 @@ class GpuExecutor:
         e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)  # noqa: E731
         self.lane_bufs = []
         self.lanes = []
+        starts, rbytes = config.pair_format == "starts", config.result_bytes
+        if config.pair_format not in ("ids", "starts"):
+            raise ValueError("pair_format must be 'ids' or 'starts'")
         for sw in strides:
-            per_read = 8 * sw + 3
-            per_pair = 12
+            per_read = 8 * sw + 3 + (4 if starts else 0)
+            per_pair = 10 if rbytes else 12
             unit = per_read + per_pair * config.pairs_per_read
             if share < unit * 16:
                 raise MemoryError(f"device budget {budget} B too small for the rings")
@@ -411,12 +436,16 @@ class GpuExecutor:
             self.lane_bufs.append(dict(
                 sw=sw, packed=e(n_reads * sw * 2, torch.int32), lens=e(n_reads, torch.int16),
                 nflag=e(n_reads, torch.uint8), pread=e(n_pairs, torch.int32), poff=e(n_pairs, torch.int32),
-                pe=e(n_pairs, torch.uint8), acc=e(n_pairs, torch.uint8), ed=e(n_pairs, torch.int16),
+                rstart=e(n_reads, torch.int32) if starts else None,
+                pe=e(n_pairs, torch.uint8), acc=e(n_pairs, torch.uint8),
+                ed=None if rbytes else e(n_pairs, torch.int16),
                 h_acc=torch.empty(n_pairs, dtype=torch.uint8, pin_memory=True),
-                h_ed=torch.empty(n_pairs, dtype=torch.int16, pin_memory=True)))
+                h_ed=None if rbytes else torch.empty(n_pairs, dtype=torch.int16, pin_memory=True)))
             lb = self.lane_bufs[-1]
-            lb["base"] = tuple(lb[x].data_ptr() for x in ("packed", "nflag", "lens", "pread", "poff", "acc", "ed"))
-            lb["h_base"] = (lb["h_acc"].data_ptr(), lb["h_ed"].data_ptr())
+            ptr = lambda t: t.data_ptr() if t is not None else 0  # noqa: E731
+            lb["base"] = tuple(ptr(lb[x]) for x in ("packed", "nflag", "lens", "rstart" if starts else "pread",
+                                                    "poff", "acc", "ed"))
+            lb["h_base"] = (ptr(lb["h_acc"]), ptr(lb["h_ed"]))
         # the single-lane view the scheduler's tests and callers read
         self.sw = strides[0]
         self.n_read_slots, self.n_pair_slots = self.lanes[0][1], self.lanes[0][2]
@@ -424,14 +453,19 @@ class GpuExecutor:
         self.packed, self.lens, self.nflag = b0["packed"], b0["lens"], b0["nflag"]
         self.pread, self.poff, self.pe, self.acc, self.ed = b0["pread"], b0["poff"], b0["pe"], b0["acc"], b0["ed"]
         self.h_acc, self.h_ed = b0["h_acc"], b0["h_ed"]
-        self.ring_bytes = sum(nr * (8 * sw + 3) + npr * 12 for sw, nr, npr in self.lanes)
+        self.ring_bytes = sum(nr * (8 * sw + 3 + (4 if starts else 0)) + npr * (10 if rbytes else 12)
+                              for sw, nr, npr in self.lanes)
         self.streams = [torch.cuda.Stream(dev) for _ in range(config.n_streams)]
         self.ws = [e(ws_bytes, torch.uint8) for _ in range(config.n_streams)]
         self.max_req_per_round = max_req = 65536
-        # per stream slot: seg_end | seg_delta (int64) and seg_e (uint8), host staging and device copies
-        self.h_seg = [torch.empty(2 * max_req, dtype=torch.int64, pin_memory=True) for _ in self.streams]
+        # per stream slot, host staging and device copies of the segment
+        # tables: int64 pair ends | read-id deltas (ids) or read ends | read
+        # slots (starts), uint32 start bases, uint8 thresholds
+        self.h_seg = [torch.empty(3 * max_req, dtype=torch.int64, pin_memory=True) for _ in self.streams]
+        self.h_segb = [torch.empty(max_req, dtype=torch.int32, pin_memory=True) for _ in self.streams]
         self.h_sege = [torch.empty(max_req, dtype=torch.uint8, pin_memory=True) for _ in self.streams]
-        self.d_seg = [e(2 * max_req, torch.int64) for _ in self.streams]
+        self.d_seg = [e(3 * max_req, torch.int64) for _ in self.streams]
+        self.d_segb = [e(max_req, torch.int32) for _ in self.streams]
         self.d_sege = [e(max_req, torch.uint8) for _ in self.streams]
         # per stream slot: gk_gather tables (dst | src | bytes), pinned so the kernel reads them directly
         self.h_gather = [torch.empty(3 * config.gather_entries, dtype=torch.int64, pin_memory=True)
@@ -452,7 +486,9 @@ class GpuExecutor:
         if len(batch) > M:
             raise ValueError("too many requests in one round")
         hseg = self.h_seg[slot].numpy()
+        hsegb = self.h_segb[slot].numpy().view(np.uint32)
         hsege = self.h_sege[slot].numpy()
+        starts = self.cfg.pair_format == "starts"
         by_lane = collections.defaultdict(list)
         for r in batch:
             by_lane[max(r.lane, 0)].append(r)
@@ -469,9 +505,9 @@ class GpuExecutor:
             npr = np.fromiter((r.n_pairs for r in reqs), np.int64, n)
             ptr = np.array([r.host_ptrs for r in reqs], np.int64).reshape(n, 5)
             base = b["base"]
+            link = (base[3] + 4 * rs, 4 * nr) if starts else (base[3] + 4 * ps, 4 * npr)
             for c, (dd, nn) in enumerate(((base[0] + rs * sw8, nr * sw8), (base[1] + rs, nr),
-                                          (base[2] + 2 * rs, 2 * nr), (base[3] + 4 * ps, 4 * npr),
-                                          (base[4] + 4 * ps, 4 * npr))):
+                                          (base[2] + 2 * rs, 2 * nr), link, (base[4] + 4 * ps, 4 * npr))):
                 d, s_, z = merge_ranges(dd, ptr[:, c], nn)
                 dst.append(d)
                 src.append(s_)
@@ -481,39 +517,61 @@ class GpuExecutor:
             brk = np.ones(n, bool)
             brk[1:] = ps[1:] != ps[:-1] + npr[:-1]
             run_id = np.cumsum(brk) - 1
-            starts = np.flatnonzero(brk)
             csum = np.cumsum(npr)
             before = np.concatenate([[0], csum[:-1]])
-            hseg[k:k + n] = csum - before[starts][run_id]
-            hseg[M + k:M + k + n] = rs - np.fromiter((r.read_base for r in reqs), np.int64, n)
+            run0 = np.flatnonzero(brk)
+            hseg[k:k + n] = csum - before[run0][run_id]
+            if starts:
+                rsum = np.cumsum(nr)
+                rbefore = np.concatenate([[0], rsum[:-1]])
+                hseg[M + k:M + k + n] = rsum - rbefore[run0][run_id]
+                hseg[2 * M + k:2 * M + k + n] = rs
+                hsegb[k:k + n] = np.fromiter((r.start_base & 0xFFFFFFFF for r in reqs), np.uint32, n)
+            else:
+                hseg[M + k:M + k + n] = rs - np.fromiter((r.read_base for r in reqs), np.int64, n)
             hsege[k:k + n] = np.fromiter((r.e for r in reqs), np.uint8, n)
-            ends = np.concatenate([starts[1:], [n]])
-            run_pairs = np.add.reduceat(npr, starts)
-            runs = [(int(ps[a]), int(cnt), k + int(a), int(e - a)) for a, e, cnt in zip(starts, ends, run_pairs)]
+            ends = np.concatenate([run0[1:], [n]])
+            run_pairs = np.add.reduceat(npr, run0)
+            run_reads = np.add.reduceat(nr, run0)
+            runs = [(int(ps[a]), int(cnt), k + int(a), int(e - a), int(rc))
+                    for a, e, cnt, rc in zip(run0, ends, run_pairs, run_reads)]
             plans.append((lane, runs))
             k += n
-        dseg, dsege = self.d_seg[slot], self.d_sege[slot]
+        dseg, dsegb, dsege = self.d_seg[slot], self.d_segb[slot], self.d_sege[slot]
         seg_ptr = self.h_seg[slot].data_ptr()
-        dst.append(np.array([dseg.data_ptr(), dseg.data_ptr() + 8 * M, dsege.data_ptr()], np.int64))
-        src.append(np.array([seg_ptr, seg_ptr + 8 * M, self.h_sege[slot].data_ptr()], np.int64))
-        nb.append(np.array([8 * k, 8 * k, k], np.int64))
+        dst.append(np.array([dseg.data_ptr(), dseg.data_ptr() + 8 * M, dseg.data_ptr() + 16 * M,
+                             dsegb.data_ptr(), dsege.data_ptr()], np.int64))
+        src.append(np.array([seg_ptr, seg_ptr + 8 * M, seg_ptr + 16 * M, self.h_segb[slot].data_ptr(),
+                             self.h_sege[slot].data_ptr()], np.int64))
+        nb.append(np.array([8 * k, 8 * k, 8 * k if starts else 0, 4 * k if starts else 0, k], np.int64))
         dst, src, nb = (np.concatenate(x).astype(np.uint64) for x in (dst, src, nb))
         self.copies_last_round = int(dst.shape[0])
         self._copy_in(dst, src, nb, slot, st)
         out_d, out_s, out_n = [], [], []
+        rbytes = self.cfg.result_bytes
+        flags = gk.GK_FLAG_RESULT_BYTE if rbytes else 0
         for lane, runs in plans:
             b = self.lane_bufs[lane]
             nr = self.lanes[lane][1]
-            for p0, np_, k0, ns in runs:
-                gk.gk_rebase_pairs(b["pread"][p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
-                                   pair_e=b["pe"][p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
+            for p0, np_, k0, ns, nrr in runs:
+                if starts:
+                    gk.gk_expand_pairs(b["pread"][p0:p0 + np_], b["pe"][p0:p0 + np_], b["rstart"],
+                                       dseg[M + k0:M + k0 + ns], dseg[k0:k0 + ns], dseg[2 * M + k0:2 * M + k0 + ns],
+                                       dsegb[k0:k0 + ns], dsege[k0:k0 + ns], n_reads=nrr, stream=st)
+                else:
+                    gk.gk_rebase_pairs(b["pread"][p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
+                                       pair_e=b["pe"][p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
                 gk.gk_filter_batched(self.ref, b["packed"], b["sw"], nr, b["lens"], b["nflag"],
                                      b["pread"][p0:p0 + np_], b["poff"][p0:p0 + np_], b["pe"][p0:p0 + np_],
-                                     self.tiling, self.ws[slot], accept=b["acc"][p0:p0 + np_],
-                                     edits=b["ed"][p0:p0 + np_], stream=st)
-                out_d += [b["h_base"][0] + p0, b["h_base"][1] + 2 * p0]
-                out_s += [b["base"][5] + p0, b["base"][6] + 2 * p0]
-                out_n += [np_, 2 * np_]
+                                     self.tiling, self.ws[slot], flags=flags, accept=b["acc"][p0:p0 + np_],
+                                     edits=None if rbytes else b["ed"][p0:p0 + np_], stream=st)
+                out_d.append(b["h_base"][0] + p0)
+                out_s.append(b["base"][5] + p0)
+                out_n.append(np_)
+                if not rbytes:
+                    out_d.append(b["h_base"][1] + 2 * p0)
+                    out_s.append(b["base"][6] + 2 * p0)
+                    out_n.append(2 * np_)
         ev_dev = torch.cuda.Event(enable_timing=True)
         ev_dev.record(st)
         if out_n:
@@ -552,8 +610,11 @@ class GpuExecutor:
         return self.ev0.elapsed_time(handle[0]) * 1e-3
 
     def results(self, r: Request):
+        """(accept, edits) of a completed request, or (result bytes, None)."""
         b = self.lane_bufs[max(r.lane, 0)]
         a = b["h_acc"].numpy()[r.pair_slot:r.pair_slot + r.n_pairs].copy()
+        if b["h_ed"] is None:
+            return a, None
         e = b["h_ed"].numpy()[r.pair_slot:r.pair_slot + r.n_pairs].view(np.uint16).copy()
         return a, e
 
@@ -570,16 +631,20 @@ class RequestPool:
     as requests received back to back into a pinned buffer would lie; their
     pair ids then number the pool's reads (read_base set accordingly) so that
     consecutive requests' arrays continue each other.  Otherwise a request
-    starts at ``start_read`` and its ids count from its first read."""
+    starts at ``start_read`` and its ids count from its first read.
+    pair_format: "ids" (a read id per pair) or "starts" (a start per read,
+    the pool's own numbering with start_base set when sequential)."""
 
     def __init__(self, ref_ascii: np.ndarray, lengths=(100, 150, 250), reads_per_len: int = 260_000,
                  cands: int = 4, stride_words: int | None = 8, seed: int = 2103_14978 + 4, pin: bool = True,
-                 keep_ascii: bool = False, sequential: bool = False):
+                 keep_ascii: bool = False, sequential: bool = False, pair_format: str = "ids"):
         import torch
 
         from . import gk, synth
 
-        self.cands, self.pin, self.sequential = cands, pin, sequential
+        if pair_format not in ("ids", "starts"):
+            raise ValueError("pair_format must be 'ids' or 'starts'")
+        self.cands, self.pin, self.sequential, self.pair_format = cands, pin, sequential, pair_format
         self.sw = stride_words if stride_words is not None else 8
         self.by_len = {}
         self.cursor = {}
@@ -599,8 +664,11 @@ class RequestPool:
         # The pool's pairs are grouped by read, `cands` per read, so the ids of
         # any slice relative to its first read are k // cands: one array serves
         # every request.
-        max_pairs = cands * max(p["lens"][1].shape[0] for p in self.by_len.values())
+        max_reads = max(p["lens"][1].shape[0] for p in self.by_len.values())
+        max_pairs = cands * max_reads
         self.rel_ids = self._pin(pin, a=(np.arange(max_pairs, dtype=np.uint32) // cands))["a"]
+        # Read k's first pair is cands * k, in the pool and in any cut (minus its base).
+        self.rel_starts = self._pin(pin, a=(np.arange(max_reads, dtype=np.uint32) * cands))["a"]
 
     @staticmethod
     def _pin(pin, **arrays):
@@ -641,14 +709,22 @@ class RequestPool:
         r1 = r0 + n_reads
         n = n_reads * self.cands
         w2 = p["sw"] * 2
-        if self.sequential:  # the pool's own ids: consecutive requests' id arrays continue each other
+        ids = starts = None
+        base = sbase = 0
+        if self.pair_format == "starts":
+            if self.sequential:  # the pool's numbering: consecutive requests' starts continue each other
+                starts, sbase = self.rel_starts[1][r0:r1], r0 * self.cands
+            else:
+                starts = self.rel_starts[1][:n_reads]
+        elif self.sequential:  # the pool's own ids: consecutive requests' id arrays continue each other
             ids, base = p["pair_read"][1][r0 * self.cands:r1 * self.cands], r0
         else:
-            ids, base = self.rel_ids[1][:n], 0
+            ids = self.rel_ids[1][:n]
         return Request(id=rid, packed=p["packed"][1][r0 * w2:r1 * w2], nflag=p["nflag"][1][r0:r1],
                        lens=p["lens"][1][r0:r1], pair_read=ids,
                        pair_off=p["pair_off"][1][r0 * self.cands:r1 * self.cands], e=e, arrival=arrival,
-                       max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None, read_base=base)
+                       max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None, read_base=base,
+                       read_start=starts, start_base=sbase)
 
 
 def poisson_plan(n_requests: int, rate_per_s: float, seed: int, size_lo=1_000, size_hi=1_000_000,

@@ -126,6 +126,15 @@ def test_pipe_rejects_bad_arguments_on_host(libgk):
     L.gk_pipe_destroy(None)  # ignored
 
 
+def test_expand_pairs_host_checks(libgk):
+    """gk_expand_pairs: nothing to do for no pairs; a missing table is
+    rejected before any device work."""
+    L = libgk.lib()
+    assert L.gk_expand_pairs(None, None, 0, None, None, None, None, None, None, 0, 0, None) == libgk.GK_OK
+    assert L.gk_expand_pairs(None, None, 10, None, None, None, None, None, None, 1, 3, None) == libgk.GK_EINVAL
+    assert b"gk_expand_pairs" in L.gk_last_error()
+
+
 def test_sliced_sizes_and_host_checks(libgk):
     """gk_sliced_bytes follows the documented layout; gk_slice and
     gk_filter_sliced reject bad arguments before any device work."""

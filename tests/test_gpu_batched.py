@@ -78,6 +78,28 @@ def test_batched_modes_and_variants():
         assert_same(got, oracle_run(w, e), f"batched scalar e={e}")
 
 
+def test_batched_result_bytes():
+    """GK_FLAG_RESULT_BYTE with per-pair thresholds 0..255: one byte per
+    pair (count capped at GK_RESULT_MAX_COUNT, GK_RESULT_UNDEFINED,
+    GK_RESULT_INVALID) equal to the oracle's counts in that format, with N
+    and invalid pairs, and no edits buffer."""
+    w = mixed_workload(34, n_pairs=20000, m=(20, 300), n_frac=0.001, read_n_frac=0.001)
+    w.pair_read[:50] = w.n_reads + 7
+    b = Batched(w)
+    ws = torch.empty(gk.gk_filter_batched_workspace(w.n_pairs), dtype=torch.uint8, device="cuda")
+    res, none = gk.gk_filter_batched(b.ref, b.reads.packed, b.reads.stride_words, b.reads.n_reads, b.read_len,
+                                     b.reads.nflag, b.pairs.pair_read, b.pairs.pair_off, b.pairs.pair_e,
+                                     gk.Tiling(3, 256, 2, 8), ws, flags=gk.GK_FLAG_RESULT_BYTE)
+    torch.cuda.synchronize()
+    assert none is None
+    _, e = oracle_run(w)
+    e = e.astype(np.int64)
+    want = np.where(e == O.UNDEFINED, gk.GK_RESULT_UNDEFINED,
+                    np.where(e == O.INVALID, gk.GK_RESULT_INVALID, np.minimum(e, gk.GK_RESULT_MAX_COUNT)))
+    assert np.array_equal(res.cpu().numpy(), want.astype(np.uint8))
+    assert (e == O.UNDEFINED).sum() > 50 and (e == O.INVALID).sum() >= 50
+
+
 def test_batched_undefined_and_invalid():
     w = mixed_workload(33, n_pairs=20000, m=(20, 300), n_frac=0.001, read_n_frac=0.001)
     rng = np.random.default_rng(6)

@@ -26,12 +26,117 @@ def requests(pool, n, rate, seed, size_hi=200_000):
     return [pool.request(p["id"], p["m"], p["e"], p["n_pairs"], p["start"], p["arrival"]) for p in plan]
 
 
+def ids_of(r):
+    """The request's pair -> read index (0-based within the request), from
+    either form: read ids, or per-read starts (CSR) written out one by one."""
+    if r.pair_read is not None:
+        return (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
+    rel = r.read_start.astype(np.int64) - r.start_base
+    ends = np.append(rel[1:], r.n_pairs)
+    out = np.empty(r.n_pairs, np.uint32)
+    for k in range(r.n_reads):
+        out[rel[k]:ends[k]] = k
+    return out
+
+
 def oracle_of(ref, r):
     rows = np.ascontiguousarray(r.ascii).reshape(-1)
     starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-    ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
-    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, ids, r.pair_off, r.e)
+    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, ids_of(r), r.pair_off, r.e)
     return a, e
+
+
+def result_bytes_of(a, e):
+    """The documented result byte of an oracle (accept, count) pair."""
+    e = e.astype(np.int64)
+    return np.where(e == 0xFFFF, gk.GK_RESULT_UNDEFINED,
+                    np.where(e == 0xFFFE, gk.GK_RESULT_INVALID, np.minimum(e, gk.GK_RESULT_MAX_COUNT))).astype(np.uint8)
+
+
+def test_read_starts_and_result_bytes_equal_the_oracle(setup):
+    """Pairs sent as one start per read (expanded on the device), results
+    returned as one byte per pair, three streams, lanes per stride: every
+    checked request's result bytes equal the oracle's counts in that format,
+    and the mix equals the same requests served with read ids."""
+    ref, gkref, _ = setup
+    out = {}
+    for fmt, rb in (("starts", True), ("ids", False)):
+        pool = serve.RequestPool(ref, lengths=(100, 150, 250), reads_per_len=60_000, stride_words=None,
+                                 keep_ascii=True, sequential=True, pair_format=fmt)
+        cfg = serve.ServeConfig(mem_cap_bytes=3 << 30, max_round_pairs=2_000_000, lanes=(4, 5, 8), n_streams=3,
+                                pair_format=fmt, result_bytes=rb)
+        ex = serve.GpuExecutor(gkref, cfg)
+        reqs = requests(pool, 300, 20_000.0, 65)
+        srv = serve.Server(ex, cfg)
+        srv.run(reqs)
+        assert all(r.status == "done" for r in reqs)
+        assert max(srv.coalesced) > 10
+        out[fmt] = reqs
+    for r in sorted(out["starts"], key=lambda q: q.n_pairs)[:30] + out["starts"][::30]:
+        assert r.edits is None
+        a, e = oracle_of(ref, r)
+        assert np.array_equal(result_bytes_of(a, e), r.accept), r.id
+    for r, q in zip(out["starts"], out["ids"]):
+        assert np.array_equal(r.accept, result_bytes_of(q.accept, q.edits)), r.id
+
+
+def test_expand_pairs_writes_every_pair_once():
+    """gk_expand_pairs: segments at scattered read rows with start bases,
+    reads with 0..7 candidates, a malformed segment (starts decreasing and
+    past its pairs): ids and thresholds equal the CSR definition, unclaimed
+    pairs get 0xFFFFFFFF (no two reads claim one pair: the definition's
+    ranges here never overlap)."""
+    require_gpu()
+    rng = np.random.default_rng(12)
+    n_rows = 5000
+    read_start = np.zeros(n_rows, np.uint32)
+    seg_read_end, seg_pair_end, seg_slot, seg_base, seg_e = [], [], [], [], []
+    want_id, want_e = [], []
+    slot, r_tot, p_tot = 7, 0, 0
+    for i in range(40):
+        nr = int(rng.integers(0, 60))
+        counts = rng.integers(0, 8, nr)
+        base = int(rng.integers(0, 1 << 32))
+        rel = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64) if nr else np.zeros(0, np.int64)
+        npairs = int(counts.sum())
+        ids = np.repeat(np.arange(slot, slot + nr), counts).astype(np.uint32)
+        if i == 17:  # malformed: the first read starts at 2 (pairs 0, 1 unclaimed), the last past the end
+            nr = max(nr, 4)
+            counts = rng.integers(2, 8, nr)
+            rel = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+            npairs = int(counts.sum())
+            rel[0] = 2
+            rel[-1] = npairs + 5
+            ids = np.full(npairs, 0xFFFFFFFF, np.uint32)
+            for k in range(nr):
+                lo = min(rel[k], npairs)
+                hi = min(rel[k + 1] if k + 1 < nr else npairs, npairs)
+                ids[lo:hi] = slot + k
+        read_start[slot:slot + nr] = (rel + base) & 0xFFFFFFFF
+        e = int(rng.integers(0, 256))
+        want_id.append(ids)
+        want_e.append(np.full(npairs, e, np.uint8))
+        r_tot += nr
+        p_tot += npairs
+        seg_read_end.append(r_tot)
+        seg_pair_end.append(p_tot)
+        seg_slot.append(slot)
+        seg_base.append(base)
+        seg_e.append(e)
+        slot += nr + int(rng.integers(0, 5))
+    want_id, want_e = np.concatenate(want_id), np.concatenate(want_e)
+    d = lambda a, dt: torch.from_numpy(np.asarray(a).astype(dt)).cuda()  # noqa: E731
+    pread = torch.zeros(p_tot, dtype=torch.int32, device="cuda")
+    pe = torch.zeros(p_tot, dtype=torch.uint8, device="cuda")
+    gk.gk_expand_pairs(pread, pe, d(read_start.view(np.int32), np.int32), d(seg_read_end, np.int64),
+                       d(seg_pair_end, np.int64), d(seg_slot, np.int64),
+                       d(np.array(seg_base, np.uint64).astype(np.uint32).view(np.int32), np.int32),
+                       d(seg_e, np.uint8), n_reads=r_tot)
+    torch.cuda.synchronize()
+    got = pread.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, want_id)
+    claimed = want_id != 0xFFFFFFFF
+    assert np.array_equal(pe.cpu().numpy()[claimed], want_e[claimed])
 
 
 def test_lanes_merged_copies_equal_the_oracle(setup):

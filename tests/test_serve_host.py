@@ -46,6 +46,15 @@ def test_fifo_ring_wraps_and_frees():
     assert ring.alloc(4) == 2
 
 
+def ids_of(r):
+    """Pair -> read index within the request, from read ids or per-read starts."""
+    if r.pair_read is not None:
+        return (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
+    rel = r.read_start.astype(np.int64) - r.start_base
+    ends = np.append(rel[1:], r.n_pairs)
+    return np.repeat(np.arange(r.n_reads, dtype=np.uint32), ends - rel)
+
+
 class FakeExecutor:
     """Completes a round `delay` simulated seconds after its launch; results
     from the oracle on the request's own reads and the genome."""
@@ -68,8 +77,7 @@ class FakeExecutor:
         for r in batch:
             rows = np.ascontiguousarray(r.ascii).reshape(-1)
             starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-            ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
-            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, ids, r.pair_off, r.e)
+            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, ids_of(r), r.pair_off, r.e)
             self.out[r.id] = (a, e)
         return self.now + self.delay
 
@@ -271,3 +279,37 @@ def test_lanes_admit_by_row_stride_and_sequential_cuts_continue():
         ids = (r.pair_read.astype(np.int64) - r.read_base).astype(np.uint32)
         a, e, _ = O.filter_batch(rows, starts, r.lens, ref, ids, r.pair_off, r.e)
         assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits)
+
+
+def test_read_starts_requests_validate_continue_and_serve():
+    """A request names its pairs' reads by ids or by per-read starts, not
+    both; a sequential pool's start arrays continue each other with the
+    start base of their first pair; a server in the starts format serves
+    them (results equal the oracle) and turns away requests of the other
+    format."""
+    ref = synth.reference(300_000, 21, 0.05, 0.0)
+    pool = serve.RequestPool(ref, lengths=(100,), reads_per_len=3000, stride_words=4, pin=False,
+                             keep_ascii=True, sequential=True, pair_format="starts")
+    a = pool.request(0, 100, 3, 400, 0, 0.0)
+    b = pool.request(1, 100, 5, 1000, 0, 0.001)
+    assert a.pair_read is None and a.start_base == 0 and a.read_start[0] == 0
+    assert b.start_base == a.n_pairs and b.read_start[0] == a.n_pairs
+    assert b.read_start.ctypes.data == a.read_start.ctypes.data + a.read_start.nbytes
+    with pytest.raises(ValueError):
+        serve.Request(9, a.packed, a.nflag, a.lens, None, a.pair_off, 3)
+    with pytest.raises(ValueError):
+        serve.Request(9, a.packed, a.nflag, a.lens, np.zeros(a.n_pairs, np.uint32), a.pair_off, 3,
+                      read_start=a.read_start)
+    ids_pool = serve.RequestPool(ref, lengths=(100,), reads_per_len=3000, stride_words=4, pin=False,
+                                 keep_ascii=True)
+    other = ids_pool.request(2, 100, 4, 500, 0, 0.002)
+    ex = FakeExecutor(ref, 100_000, 400_000)
+    srv = serve.Server(ex, serve.ServeConfig(stride_words=4, max_read_len=128, pair_format="starts"))
+    srv.run([a, b, other], clock=SimClock(ex), idle_sleep=0)
+    assert a.status == b.status == "done" and other.status == "rejected"
+    for r in (a, b):
+        rows = np.ascontiguousarray(r.ascii).reshape(-1)
+        starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
+        want = O.filter_batch(rows, starts, r.lens, ref, (np.arange(r.n_pairs) // 4).astype(np.uint32),
+                              r.pair_off, r.e)
+        assert np.array_equal(want[0], r.accept) and np.array_equal(want[1], r.edits)
