@@ -608,7 +608,24 @@ def run_mine(args):
                     "word_ops_x_alu_peak": survey_ops / (t * 1e-3) / 1e12 / ALU_PEAK_TOPS,
                     "note": "per-filtration counts (every threshold reading its inputs and building its masks "
                             "anew); the sweep shares both across the thresholds, so these exceed 1"},
-                "encode_ms": encode_ms, "slice_ms": slice_ms}
+                "encode_ms": encode_ms, "slice_ms": slice_ms,
+                "step": step_roofline(roof_ms, encode_ms + slice_ms + t, slice_pass=True)}
+
+    W_m = -(-m // 32)
+    enc_bytes = w.n_reads * (m + 8 * W_m + 1)  # ASCII rows in, planes + N flag out
+
+    def step_roofline(kernels_roof_ms, measured_ms, slice_pass=False):
+        """The whole step against its roofline time: the filter launches'
+        roofline plus the encoder's bytes (and the slice pass's: the pair's
+        inputs read, the planes written) at the HBM peak."""
+        extra = enc_bytes
+        if slice_pass:
+            extra += w.n_pairs * (bytes_per_pair(m, c, False) - 3 + sliced_bytes_per_pair(m) - 3)
+        roof = kernels_roof_ms + 1e3 * extra / (hbm_peak * 1e9)
+        return {"roofline_ms": roof, "measured_ms": measured_ms, "frac": roof / measured_ms,
+                "basis": "filter launches at the slower of their ops (ALU peak) and bytes (HBM peak), plus "
+                         "the encoder's bytes" + (" and the slice pass's bytes" if slice_pass else "") +
+                         " at the HBM peak"}
 
     def pp_sweep_roofline(sweep_ms, encode_ms):
         """The per-pair sweep launch: its algorithmic ops (pp_sweep_ops_per_pair)
@@ -639,7 +656,9 @@ def run_mine(args):
                     "word_ops_x_alu_peak": survey_ops / (sweep_ms * 1e-3) / 1e12 / ALU_PEAK_TOPS,
                     "note": "per-filtration counts (every threshold reading its inputs and building its masks "
                             "anew); the sweep shares both across the thresholds, so these exceed 1"},
-                "encode_ms": encode_ms}
+                "encode_ms": encode_ms,
+                "step": step_roofline(1e3 * max(ops / (ALU_PEAK_TOPS * 1e12), bts / (hbm_peak * 1e9)),
+                                      encode_ms + sweep_ms)}
 
     probe = probe_alu(torch, gk, stream, args.probe_all)
     clocks = ClockSampler(uuid)
