@@ -279,7 +279,7 @@ __device__ __forceinline__ uint32_t filter_loaded(const FilterArgs &a, const Pai
 // count K, each against its own window: the read's +k and -k copies (4W
 // funnel shifts per step) are built once for all NP windows.  rh/rl and
 // gh/gl are the read's and the windows' planes, zero past m.
-template <int W, int NP>
+template <int W, int NP, bool DIRECT = false>
 __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m, uint32_t K,
                                                 const uint32_t (&rh)[W], const uint32_t (&rl)[W],
                                                 const uint32_t (&gh)[NP][W], const uint32_t (&gl)[NP][W],
@@ -302,11 +302,18 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     for (int w = 0; w < W; ++w) acc[j][w] = dil(d, w);  // shift 0
   }
   {
+    // DIRECT (a shift count fixed at compile time): the read's +k and -k
+    // copies come straight from rh/rl by k-base funnel shifts, no copy carried
+    // from step to step (fewer live registers: measured faster at K = 0..2);
+    // otherwise each step moves the carried copies by one base (faster for a
+    // runtime K and in the sweep).
     uint32_t ph[W], pl[W], nh[W], nl[W];
+    if (!DIRECT) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      ph[w] = nh[w] = rh[w];
-      pl[w] = nl[w] = rl[w];
+      for (int w = 0; w < W; ++w) {
+        ph[w] = nh[w] = rh[w];
+        pl[w] = nl[w] = rl[w];
+      }
     }
     // The vacated positions of each shifted mask are ORed into its difference
     // vector before the dilation: dil(d | V) = dil(d) | dil(V), the mask ORed
@@ -315,15 +322,25 @@ __device__ __forceinline__ void deferred_counts(const FilterArgs &a, uint32_t m,
     uint32_t tv_hi = ~lastmask;       // mask -k: positions >= m-k (and >= m), top word
     uint32_t tv_lo = 0u;              // and the word below it
     for (uint32_t k = 1; k <= K; ++k) {
+      if (DIRECT) {
 #pragma unroll
-      for (int w = W - 1; w >= 0; --w) {
-        ph[w] = __funnelshift_l(w > 0 ? ph[w - 1] : 0u, ph[w], 1);
-        pl[w] = __funnelshift_l(w > 0 ? pl[w - 1] : 0u, pl[w], 1);
-      }
+        for (int w = 0; w < W; ++w) {
+          ph[w] = __funnelshift_l(w > 0 ? rh[w - 1] : 0u, rh[w], k);
+          pl[w] = __funnelshift_l(w > 0 ? rl[w - 1] : 0u, rl[w], k);
+          nh[w] = __funnelshift_r(rh[w], w + 1 < W ? rh[w + 1] : 0u, k);
+          nl[w] = __funnelshift_r(rl[w], w + 1 < W ? rl[w + 1] : 0u, k);
+        }
+      } else {
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
-        nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
+        for (int w = W - 1; w >= 0; --w) {
+          ph[w] = __funnelshift_l(w > 0 ? ph[w - 1] : 0u, ph[w], 1);
+          pl[w] = __funnelshift_l(w > 0 ? pl[w - 1] : 0u, pl[w], 1);
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          nh[w] = __funnelshift_r(nh[w], w + 1 < W ? nh[w + 1] : 0u, 1);
+          nl[w] = __funnelshift_r(nl[w], w + 1 < W ? nl[w + 1] : 0u, 1);
+        }
       }
       lead = 2u * lead + 1u;
       tv_lo = __funnelshift_r(tv_lo, tv_hi, 1);
@@ -646,11 +663,11 @@ __device__ __forceinline__ void pair_planes(const PairData<W> &x, uint32_t (&rh)
   gl[W - 1] &= lastmask;
 }
 
-template <int W>
+template <int W, bool DIRECT = false>
 __device__ __forceinline__ uint32_t filter_loaded_deferred(const FilterArgs &a, const PairData<W> &x) {
   uint32_t rh[W], rl[W], gh[1][W], gl[1][W], count[1];
   pair_planes<W>(x, rh, rl, gh[0], gl[0]);
-  deferred_counts<W, 1>(a, x.m, min(x.e, x.m - 1), rh, rl, gh, gl, count);
+  deferred_counts<W, 1, DIRECT>(a, x.m, min(x.e, x.m - 1), rh, rl, gh, gl, count);
   return count[0];
 }
 
@@ -730,8 +747,9 @@ __device__ __forceinline__ void filter_and_write(const FilterArgs &a, uint64_t p
   if constexpr (VARIANT == 3) {
     sweep_and_write<W>(a, p, x);
   } else {
-    const uint32_t count = VARIANT == 2 || VARIANT == 4 ? filter_loaded_deferred<W>(a, x)
-                                                        : filter_loaded<W, VARIANT == 1>(a, x);
+    const uint32_t count = VARIANT == 4   ? filter_loaded_deferred<W, true>(a, x)
+                           : VARIANT == 2 ? filter_loaded_deferred<W>(a, x)
+                                          : filter_loaded<W, VARIANT == 1>(a, x);
     write_count(a, p, count, x.e);
   }
 }
@@ -1041,7 +1059,7 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
                                   });
     } else {
       const uint32_t K = KC >= 0 ? (uint32_t)KC : min(a.fixed_e, a.m - 1);
-      deferred_counts<W, 2>(a, a.m, K, rh, rl, gh, gl, count);
+      deferred_counts<W, 2, (KC >= 0)>(a, a.m, K, rh, rl, gh, gl, count);
       write_count(a, p0, count[0], a.fixed_e);
       write_count(a, p1, count[1], a.fixed_e);
     }
