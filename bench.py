@@ -1114,7 +1114,7 @@ def measure_c5(args) -> dict:
     # cuts, rows at each length's own stride); the server has one lane per
     # stride.
     pool = serve.RequestPool(ref, lengths=lengths, reads_per_len=260_000, stride_words=None, sequential=True,
-                             pair_format="starts")
+                             pair_format="starts", compact_reads=True)
     lanes = tuple(sorted({pool.by_len[m]["sw"] for m in lengths}))
     stream = torch.cuda.current_stream()
     per_combo = {}  # the plain filter on the mix, every (m, e) equally likely
@@ -1161,7 +1161,9 @@ def measure_c5(args) -> dict:
     for load in (0.5, 0.8, 0.95):
         levels[str(load)] = level(load * capacity, args.level_seconds, 2103_14978 + 5 + int(load * 100))
         levels[str(load)]["load"] = load
-    h2d_pp = float(np.mean([(8 * pool.by_len[m]["sw"] + 2 + 1 + 4) / pool.cands + 4 for m in lengths]))
+    # per read: packed row + start (one length per request; N flags only for
+    # requests with an N read, none in this pool's reads)
+    h2d_pp = float(np.mean([(8 * pool.by_len[m]["sw"] + 4) / pool.cands + 4 for m in lengths]))
     ok = all(abs(v["served_gpairs_s"] / v["offered_gpairs_s"] - 1) < 0.05 for v in levels.values())
     mono = levels["0.5"]["p99_ms"] <= levels["0.8"]["p99_ms"] <= levels["0.95"]["p99_ms"]
     gkref.close()
@@ -1177,9 +1179,10 @@ def measure_c5(args) -> dict:
             "copies_per_round_last": ex.copies_last_round,
             "streams": cfg.n_streams,
             "host_link_bytes_per_pair": {"in": h2d_pp, "out": 1.0,
-                                         "basis": "per read: packed row (8 x row words) + length 2 + N flag 1 + "
-                                                  "start 4, per pair: offset 4; 4 candidates per read, lengths "
-                                                  "100/150/250 equally likely"},
+                                         "basis": "per read: packed row (8 x row words) + start 4, per pair: "
+                                                  "offset 4; one length per request and no N flags for requests "
+                                                  "without N (written on the device); 4 candidates per read, "
+                                                  "lengths 100/150/250 equally likely"},
             "inputs": "requests received back to back into per-length pinned buffers (rows at each length's "
                       "own stride); a round's copies merge per lane and array; candidates as one start per read "
                       "(gk_expand_pairs), results as one byte per pair (GK_FLAG_RESULT_BYTE)"}

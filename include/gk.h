@@ -389,16 +389,25 @@ int gk_rebase_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs,
  *   seg_e          device, n_segs uint8 thresholds
  *   read_start     device, uint32 per read-buffer row: the start value of the
  *                  read in that row
+ *   seg_read_info  device, n_segs uint32, or NULL: bits 0..15 a read length
+ *                  shared by all of segment i's reads (0: lengths given per
+ *                  read), bit GK_SEG_NO_N set when none of them holds a
+ *                  non-ACGT base; for those segments the kernel writes
+ *                  read_len / read_nflag (device, uint16 / uint8 per
+ *                  read-buffer row; NULL when no segment needs them), so
+ *                  such requests need not send these per-read arrays
  * Writes pair_read[j] = the row of the read owning pair j and pair_e[j] =
  * its segment's threshold.  Starts are clamped to the segment's pairs; a
  * pair that no read claims (starts decreasing or skipping pairs) gets id
  * 0xFFFFFFFF, which the filters report as an invalid pair.  Asynchronous on
  * `stream`.
  */
+#define GK_SEG_NO_N 0x10000u
+
 int gk_expand_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint32_t *read_start,
                     const uint64_t *seg_read_end, const uint64_t *seg_pair_end, const uint64_t *seg_read_slot,
-                    const uint32_t *seg_start_base, const uint8_t *seg_e, uint32_t n_segs, uint64_t n_reads,
-                    void *stream);
+                    const uint32_t *seg_start_base, const uint8_t *seg_e, const uint32_t *seg_read_info,
+                    uint16_t *read_len, uint8_t *read_nflag, uint32_t n_segs, uint64_t n_reads, void *stream);
 
 /*
  * gk_copy_many -- n asynchronous copies on `stream`, one cudaMemcpyAsync

@@ -33,7 +33,9 @@ __global__ void expand_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restr
                               const uint32_t *__restrict__ read_start, const uint64_t *__restrict__ seg_read_end,
                               const uint64_t *__restrict__ seg_pair_end, const uint64_t *__restrict__ seg_read_slot,
                               const uint32_t *__restrict__ seg_start_base, const uint8_t *__restrict__ seg_e,
-                              uint32_t n_segs, uint64_t n_vreads, uint64_t n_pairs) {
+                              const uint32_t *__restrict__ seg_read_info, uint16_t *__restrict__ read_len,
+                              uint8_t *__restrict__ read_nflag, uint32_t n_segs, uint64_t n_vreads,
+                              uint64_t n_pairs) {
   const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (v >= n_vreads) return;
   uint32_t lo = 0, hi = n_segs - 1;  // first segment whose read end exceeds v
@@ -50,6 +52,11 @@ __global__ void expand_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restr
   const uint64_t from = a < np ? a : np, to = b < np ? b : np;
   const uint32_t id = slot <= 0xFFFFFFFEull ? (uint32_t)slot : 0xFFFFFFFFu;
   const uint8_t e = seg_e[lo];
+  if (seg_read_info) {  // one length and / or no N for the whole segment
+    const uint32_t info = seg_read_info[lo];
+    if ((info & 0xFFFFu) && read_len) read_len[slot] = (uint16_t)(info & 0xFFFFu);
+    if ((info & GK_SEG_NO_N) && read_nflag) read_nflag[slot] = 0;
+  }
   const uint64_t end = p0 + to < n_pairs ? p0 + to : n_pairs;  // never past the launch's pairs
   for (uint64_t j = p0 + from; j < end; ++j) {
     pair_read[j] = id;
@@ -62,21 +69,24 @@ __global__ void expand_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restr
 extern "C" int gk_expand_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint32_t *read_start,
                                const uint64_t *seg_read_end, const uint64_t *seg_pair_end,
                                const uint64_t *seg_read_slot, const uint32_t *seg_start_base,
-                               const uint8_t *seg_e, uint32_t n_segs, uint64_t n_reads, void *stream) {
+                               const uint8_t *seg_e, const uint32_t *seg_read_info, uint16_t *read_len,
+                               uint8_t *read_nflag, uint32_t n_segs, uint64_t n_reads, void *stream) {
   gk::clear_error();
-  if (n_pairs == 0) return GK_OK;
+  if (n_pairs == 0 && !seg_read_info) return GK_OK;
   if (!pair_read || !pair_e || !read_start || !seg_read_end || !seg_pair_end || !seg_read_slot ||
       !seg_start_base || !seg_e || n_segs == 0)
     return gk::fail(GK_EINVAL, "gk_expand_pairs: null buffer or no segments");
   cudaStream_t st = (cudaStream_t)stream;
   // Pairs that no read claims stay invalid (an id no read has).
-  cudaError_t err = cudaMemsetAsync(pair_read, 0xFF, n_pairs * sizeof(uint32_t), st);
-  if (err != cudaSuccess) return gk::cuda_check(err, "gk_expand_pairs: fill");
+  if (n_pairs) {
+    const cudaError_t err = cudaMemsetAsync(pair_read, 0xFF, n_pairs * sizeof(uint32_t), st);
+    if (err != cudaSuccess) return gk::cuda_check(err, "gk_expand_pairs: fill");
+  }
   if (n_reads == 0) return GK_OK;
   const int threads = 256;
   expand_kernel<<<(unsigned)((n_reads + threads - 1) / threads), threads, 0, st>>>(
-      pair_read, pair_e, read_start, seg_read_end, seg_pair_end, seg_read_slot, seg_start_base, seg_e, n_segs,
-      n_reads, n_pairs);
+      pair_read, pair_e, read_start, seg_read_end, seg_pair_end, seg_read_slot, seg_start_base, seg_e,
+      seg_read_info, read_len, read_nflag, n_segs, n_reads, n_pairs);
   return gk::cuda_check(cudaGetLastError(), "gk_expand_pairs: launch");
 }
 

@@ -77,7 +77,8 @@ _SIGS = {
     "gk_rebase_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                          _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_expand_pairs": ([_c.c_void_p, _c.c_void_p, _c.c_uint64, _c.c_void_p, _c.c_void_p, _c.c_void_p,
-                         _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_uint64, _c.c_void_p], _c.c_int),
+                         _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                         _c.c_uint32, _c.c_uint64, _c.c_void_p], _c.c_int),
     "gk_copy_many": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_int, _c.c_void_p], _c.c_int),
     "gk_gather": ([_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_uint32, _c.c_void_p], _c.c_int),
     "gk_pipe_create": ([_c.c_void_p, _c.POINTER(PipeDesc), _c.POINTER(_c.c_void_p)], _c.c_int),
@@ -465,15 +466,22 @@ def gk_filter_batched_noalloc(ref: Reference, reads: torch.Tensor, stride_words:
     return accept, edits
 
 
+GK_SEG_NO_N = 0x10000
+
+
 def gk_expand_pairs(pair_read: torch.Tensor, pair_e: torch.Tensor, read_start: torch.Tensor,
                     seg_read_end: torch.Tensor, seg_pair_end: torch.Tensor, seg_read_slot: torch.Tensor,
-                    seg_start_base: torch.Tensor, seg_e: torch.Tensor, n_reads: int | None = None, stream=None):
+                    seg_start_base: torch.Tensor, seg_e: torch.Tensor, n_reads: int | None = None,
+                    seg_read_info: torch.Tensor | None = None, read_len: torch.Tensor | None = None,
+                    read_nflag: torch.Tensor | None = None, stream=None):
     """Per-pair read ids (read-buffer rows) and thresholds of the pairs of
     n_segs requests from their reads' start offsets (gk_expand_pairs):
     segment i owns reads [seg_read_end[i-1], seg_read_end[i]) at rows
     seg_read_slot[i] + k and pairs [seg_pair_end[i-1], seg_pair_end[i]);
     read_start[row] - seg_start_base[i] is the read's first pair within its
-    request.  int64 / int32 / uint8 CUDA tensors as in gk.h."""
+    request.  With ``seg_read_info`` (int32: a shared read length in bits
+    0..15, GK_SEG_NO_N) the rows' lengths and N flags of such segments are
+    written too.  int64 / int32 / uint8 CUDA tensors as in gk.h."""
     n_segs = seg_read_end.numel()
     n = pair_read.numel()
     if n_reads is None:
@@ -484,7 +492,10 @@ def gk_expand_pairs(pair_read: torch.Tensor, pair_e: torch.Tensor, read_start: t
                                  _dptr(seg_pair_end, torch.int64, "seg_pair_end", n_segs),
                                  _dptr(seg_read_slot, torch.int64, "seg_read_slot", n_segs),
                                  _dptr(seg_start_base, torch.int32, "seg_start_base", n_segs),
-                                 _dptr(seg_e, torch.uint8, "seg_e", n_segs), n_segs, n_reads, _stream(stream)))
+                                 _dptr(seg_e, torch.uint8, "seg_e", n_segs),
+                                 _dptr(seg_read_info, torch.int32, "seg_read_info", n_segs),
+                                 _dptr(read_len, torch.int16, "read_len"), _dptr(read_nflag, torch.uint8, "read_nflag"),
+                                 n_segs, n_reads, _stream(stream)))
 
 
 def gk_rebase_pairs(pair_read: torch.Tensor, seg_end: torch.Tensor, seg_delta: torch.Tensor,

@@ -56,8 +56,8 @@ class Request:
 
     id: int
     packed: np.ndarray
-    nflag: np.ndarray
-    lens: np.ndarray
+    nflag: np.ndarray | None
+    lens: np.ndarray | None
     pair_read: np.ndarray | None
     pair_off: np.ndarray
     e: int
@@ -78,6 +78,7 @@ class Request:
     lane: int = -1
     read_start: np.ndarray | None = None  # CSR form of the pairs' reads (instead of pair_read)
     start_base: int = 0                   # read_start - start_base counts from this request's first pair
+    read_len: int = 0                     # with read_start: one length for every read (lens None)
 
     def __post_init__(self):
         # Sizes and host addresses are read once here: the scheduler handles
@@ -86,7 +87,16 @@ class Request:
         # host_ptrs[3] is the pair-to-read array of either form.
         if (self.pair_read is None) == (self.read_start is None):
             raise ValueError("a request gives exactly one of pair_read and read_start")
-        self.n_reads = int(self.lens.shape[0])
+        if self.lens is None or self.nflag is None:
+            # One length for all reads and / or no N in any: the device writes
+            # the per-read values (starts form only).
+            if self.read_start is None or (self.lens is None and self.read_len <= 0):
+                raise ValueError("lens / nflag may be left out only with read_start (and read_len for lens)")
+        if self.lens is None and self.max_len < 0:
+            self.max_len = int(self.read_len)
+        self.n_reads = int(self.lens.shape[0] if self.lens is not None else self.read_start.shape[0])
+        if self.nflag is not None and self.nflag.shape[0] != self.n_reads:
+            raise ValueError("nflag needs one value per read")
         self.n_pairs = int(self.pair_off.shape[0])
         if self.pair_read is not None and self.pair_read.shape[0] != self.n_pairs:
             raise ValueError("pair_read and pair_off differ in length")
@@ -95,8 +105,11 @@ class Request:
         self.pair_format = "ids" if self.pair_read is not None else "starts"
         self.stride_words = int(self.packed.size // (2 * self.n_reads)) if self.n_reads else 0
         link = self.pair_read if self.pair_read is not None else self.read_start
-        self.host_ptrs = tuple(int(x.__array_interface__["data"][0])
+        self.host_ptrs = tuple(int(x.__array_interface__["data"][0]) if x is not None else 0
                                for x in (self.packed, self.nflag, self.lens, link, self.pair_off))
+        # the per-segment word gk_expand_pairs takes: a shared length, no N
+        self.read_info = (int(self.read_len) & 0xFFFF if self.lens is None else 0) | (
+            0x10000 if self.nflag is None else 0)
 
     def cancel(self) -> bool:
         """Cancel a request that has not been admitted yet."""
@@ -460,12 +473,13 @@ class GpuExecutor:
         self.max_req_per_round = max_req = 65536
         # per stream slot, host staging and device copies of the segment
         # tables: int64 pair ends | read-id deltas (ids) or read ends | read
-        # slots (starts), uint32 start bases, uint8 thresholds
+        # slots (starts), uint32 start bases | read info (starts), uint8
+        # thresholds
         self.h_seg = [torch.empty(3 * max_req, dtype=torch.int64, pin_memory=True) for _ in self.streams]
-        self.h_segb = [torch.empty(max_req, dtype=torch.int32, pin_memory=True) for _ in self.streams]
+        self.h_segb = [torch.empty(2 * max_req, dtype=torch.int32, pin_memory=True) for _ in self.streams]
         self.h_sege = [torch.empty(max_req, dtype=torch.uint8, pin_memory=True) for _ in self.streams]
         self.d_seg = [e(3 * max_req, torch.int64) for _ in self.streams]
-        self.d_segb = [e(max_req, torch.int32) for _ in self.streams]
+        self.d_segb = [e(2 * max_req, torch.int32) for _ in self.streams]
         self.d_sege = [e(max_req, torch.uint8) for _ in self.streams]
         # per stream slot: gk_gather tables (dst | src | bytes), pinned so the kernel reads them directly
         self.h_gather = [torch.empty(3 * config.gather_entries, dtype=torch.int64, pin_memory=True)
@@ -506,8 +520,10 @@ class GpuExecutor:
             ptr = np.array([r.host_ptrs for r in reqs], np.int64).reshape(n, 5)
             base = b["base"]
             link = (base[3] + 4 * rs, 4 * nr) if starts else (base[3] + 4 * ps, 4 * npr)
-            for c, (dd, nn) in enumerate(((base[0] + rs * sw8, nr * sw8), (base[1] + rs, nr),
-                                          (base[2] + 2 * rs, 2 * nr), link, (base[4] + 4 * ps, 4 * npr))):
+            has_nf = (ptr[:, 1] != 0).astype(np.int64)  # per-read arrays a request left out move nothing
+            has_ln = (ptr[:, 2] != 0).astype(np.int64)
+            for c, (dd, nn) in enumerate(((base[0] + rs * sw8, nr * sw8), (base[1] + rs, nr * has_nf),
+                                          (base[2] + 2 * rs, 2 * nr * has_ln), link, (base[4] + 4 * ps, 4 * npr))):
                 d, s_, z = merge_ranges(dd, ptr[:, c], nn)
                 dst.append(d)
                 src.append(s_)
@@ -527,6 +543,7 @@ class GpuExecutor:
                 hseg[M + k:M + k + n] = rsum - rbefore[run0][run_id]
                 hseg[2 * M + k:2 * M + k + n] = rs
                 hsegb[k:k + n] = np.fromiter((r.start_base & 0xFFFFFFFF for r in reqs), np.uint32, n)
+                hsegb[M + k:M + k + n] = np.fromiter((r.read_info for r in reqs), np.uint32, n)
             else:
                 hseg[M + k:M + k + n] = rs - np.fromiter((r.read_base for r in reqs), np.int64, n)
             hsege[k:k + n] = np.fromiter((r.e for r in reqs), np.uint8, n)
@@ -539,11 +556,13 @@ class GpuExecutor:
             k += n
         dseg, dsegb, dsege = self.d_seg[slot], self.d_segb[slot], self.d_sege[slot]
         seg_ptr = self.h_seg[slot].data_ptr()
+        segb_ptr = self.h_segb[slot].data_ptr()
         dst.append(np.array([dseg.data_ptr(), dseg.data_ptr() + 8 * M, dseg.data_ptr() + 16 * M,
-                             dsegb.data_ptr(), dsege.data_ptr()], np.int64))
-        src.append(np.array([seg_ptr, seg_ptr + 8 * M, seg_ptr + 16 * M, self.h_segb[slot].data_ptr(),
+                             dsegb.data_ptr(), dsegb.data_ptr() + 4 * M, dsege.data_ptr()], np.int64))
+        src.append(np.array([seg_ptr, seg_ptr + 8 * M, seg_ptr + 16 * M, segb_ptr, segb_ptr + 4 * M,
                              self.h_sege[slot].data_ptr()], np.int64))
-        nb.append(np.array([8 * k, 8 * k, 8 * k if starts else 0, 4 * k if starts else 0, k], np.int64))
+        nb.append(np.array([8 * k, 8 * k, 8 * k if starts else 0, 4 * k if starts else 0,
+                            4 * k if starts else 0, k], np.int64))
         dst, src, nb = (np.concatenate(x).astype(np.uint64) for x in (dst, src, nb))
         self.copies_last_round = int(dst.shape[0])
         self._copy_in(dst, src, nb, slot, st)
@@ -557,7 +576,9 @@ class GpuExecutor:
                 if starts:
                     gk.gk_expand_pairs(b["pread"][p0:p0 + np_], b["pe"][p0:p0 + np_], b["rstart"],
                                        dseg[M + k0:M + k0 + ns], dseg[k0:k0 + ns], dseg[2 * M + k0:2 * M + k0 + ns],
-                                       dsegb[k0:k0 + ns], dsege[k0:k0 + ns], n_reads=nrr, stream=st)
+                                       dsegb[k0:k0 + ns], dsege[k0:k0 + ns], n_reads=nrr,
+                                       seg_read_info=dsegb[M + k0:M + k0 + ns], read_len=b["lens"],
+                                       read_nflag=b["nflag"], stream=st)
                 else:
                     gk.gk_rebase_pairs(b["pread"][p0:p0 + np_], dseg[k0:k0 + ns], dseg[M + k0:M + k0 + ns],
                                        pair_e=b["pe"][p0:p0 + np_], seg_e=dsege[k0:k0 + ns], stream=st)
@@ -633,18 +654,25 @@ class RequestPool:
     consecutive requests' arrays continue each other.  Otherwise a request
     starts at ``start_read`` and its ids count from its first read.
     pair_format: "ids" (a read id per pair) or "starts" (a start per read,
-    the pool's own numbering with start_base set when sequential)."""
+    the pool's own numbering with start_base set when sequential).
+    compact_reads (starts form only): a request gives one read length
+    instead of per-read lengths, and no N flags when none of its reads holds
+    an N (as a client that knows its reads' length and content would)."""
 
     def __init__(self, ref_ascii: np.ndarray, lengths=(100, 150, 250), reads_per_len: int = 260_000,
                  cands: int = 4, stride_words: int | None = 8, seed: int = 2103_14978 + 4, pin: bool = True,
-                 keep_ascii: bool = False, sequential: bool = False, pair_format: str = "ids"):
+                 keep_ascii: bool = False, sequential: bool = False, pair_format: str = "ids",
+                 compact_reads: bool = False):
         import torch
 
         from . import gk, synth
 
         if pair_format not in ("ids", "starts"):
             raise ValueError("pair_format must be 'ids' or 'starts'")
+        if compact_reads and pair_format != "starts":
+            raise ValueError("compact_reads needs pair_format 'starts'")
         self.cands, self.pin, self.sequential, self.pair_format = cands, pin, sequential, pair_format
+        self.compact_reads = compact_reads
         self.sw = stride_words if stride_words is not None else 8
         self.by_len = {}
         self.cursor = {}
@@ -658,6 +686,8 @@ class RequestPool:
                                        lens=np.full(w.n_reads, m, np.uint16), pair_read=w.pair_read,
                                        pair_off=w.pair_off)
             self.by_len[m]["sw"] = sw
+            # N reads before each read: whether a cut holds any is two lookups
+            self.by_len[m]["n_before"] = np.concatenate([[0], np.cumsum(nflag.numpy() != 0)])
             self.cursor[m] = 0
             if keep_ascii:
                 self.by_len[m]["ascii"] = (None, w.reads.reshape(w.n_reads, w.stride))
@@ -720,11 +750,16 @@ class RequestPool:
             ids, base = p["pair_read"][1][r0 * self.cands:r1 * self.cands], r0
         else:
             ids = self.rel_ids[1][:n]
-        return Request(id=rid, packed=p["packed"][1][r0 * w2:r1 * w2], nflag=p["nflag"][1][r0:r1],
-                       lens=p["lens"][1][r0:r1], pair_read=ids,
+        lens, nflag = p["lens"][1][r0:r1], p["nflag"][1][r0:r1]
+        if self.compact_reads:
+            lens = None
+            if p["n_before"][r1] == p["n_before"][r0]:
+                nflag = None
+        return Request(id=rid, packed=p["packed"][1][r0 * w2:r1 * w2], nflag=nflag,
+                       lens=lens, pair_read=ids,
                        pair_off=p["pair_off"][1][r0 * self.cands:r1 * self.cands], e=e, arrival=arrival,
                        max_len=m, ascii=p["ascii"][1][r0:r1] if "ascii" in p else None, read_base=base,
-                       read_start=starts, start_base=sbase)
+                       read_start=starts, start_base=sbase, read_len=m if self.compact_reads else 0)
 
 
 def poisson_plan(n_requests: int, rate_per_s: float, seed: int, size_lo=1_000, size_hi=1_000_000,

@@ -130,8 +130,8 @@ def test_expand_pairs_host_checks(libgk):
     """gk_expand_pairs: nothing to do for no pairs; a missing table is
     rejected before any device work."""
     L = libgk.lib()
-    assert L.gk_expand_pairs(None, None, 0, None, None, None, None, None, None, 0, 0, None) == libgk.GK_OK
-    assert L.gk_expand_pairs(None, None, 10, None, None, None, None, None, None, 1, 3, None) == libgk.GK_EINVAL
+    assert L.gk_expand_pairs(None, None, 0, None, None, None, None, None, None, None, None, None, 0, 0, None) == libgk.GK_OK
+    assert L.gk_expand_pairs(None, None, 10, None, None, None, None, None, None, None, None, None, 1, 3, None) == libgk.GK_EINVAL
     assert b"gk_expand_pairs" in L.gk_last_error()
 
 

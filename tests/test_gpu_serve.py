@@ -21,8 +21,8 @@ def setup():
     return ref, gkref, pool
 
 
-def requests(pool, n, rate, seed, size_hi=200_000):
-    plan = serve.poisson_plan(n, rate, seed, size_lo=1_000, size_hi=size_hi)
+def requests(pool, n, rate, seed, size_hi=200_000, lengths=(100, 150, 250)):
+    plan = serve.poisson_plan(n, rate, seed, size_lo=1_000, size_hi=size_hi, lengths=lengths)
     return [pool.request(p["id"], p["m"], p["e"], p["n_pairs"], p["start"], p["arrival"]) for p in plan]
 
 
@@ -39,10 +39,14 @@ def ids_of(r):
     return out
 
 
+def lens_of(r):
+    return r.lens.view(np.uint16) if r.lens is not None else np.full(r.n_reads, r.read_len, np.uint16)
+
+
 def oracle_of(ref, r):
     rows = np.ascontiguousarray(r.ascii).reshape(-1)
     starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-    a, e, _ = O.filter_batch(rows, starts, r.lens.view(np.uint16), ref, ids_of(r), r.pair_off, r.e)
+    a, e, _ = O.filter_batch(rows, starts, lens_of(r), ref, ids_of(r), r.pair_off, r.e)
     return a, e
 
 
@@ -54,15 +58,17 @@ def result_bytes_of(a, e):
 
 
 def test_read_starts_and_result_bytes_equal_the_oracle(setup):
-    """Pairs sent as one start per read (expanded on the device), results
-    returned as one byte per pair, three streams, lanes per stride: every
-    checked request's result bytes equal the oracle's counts in that format,
-    and the mix equals the same requests served with read ids."""
+    """Pairs sent as one start per read (expanded on the device), one read
+    length per request and no N flags for requests without N (written on
+    the device), results returned as one byte per pair, three streams,
+    lanes per stride: every checked request's result bytes equal the
+    oracle's counts in that format, and the mix equals the same requests
+    served with read ids, per-read lengths and flags."""
     ref, gkref, _ = setup
     out = {}
     for fmt, rb in (("starts", True), ("ids", False)):
         pool = serve.RequestPool(ref, lengths=(100, 150, 250), reads_per_len=60_000, stride_words=None,
-                                 keep_ascii=True, sequential=True, pair_format=fmt)
+                                 keep_ascii=True, sequential=True, pair_format=fmt, compact_reads=fmt == "starts")
         cfg = serve.ServeConfig(mem_cap_bytes=3 << 30, max_round_pairs=2_000_000, lanes=(4, 5, 8), n_streams=3,
                                 pair_format=fmt, result_bytes=rb)
         ex = serve.GpuExecutor(gkref, cfg)
@@ -72,12 +78,32 @@ def test_read_starts_and_result_bytes_equal_the_oracle(setup):
         assert all(r.status == "done" for r in reqs)
         assert max(srv.coalesced) > 10
         out[fmt] = reqs
+    assert all(r.lens is None for r in out["starts"])
     for r in sorted(out["starts"], key=lambda q: q.n_pairs)[:30] + out["starts"][::30]:
         assert r.edits is None
         a, e = oracle_of(ref, r)
         assert np.array_equal(result_bytes_of(a, e), r.accept), r.id
     for r, q in zip(out["starts"], out["ids"]):
         assert np.array_equal(r.accept, result_bytes_of(q.accept, q.edits)), r.id
+
+
+def test_requests_without_n_flags_equal_the_oracle():
+    """On a genome without N every compact request leaves out its N flags
+    and its lengths; the device writes both: results equal the oracle."""
+    require_gpu()
+    ref = synth.reference(4_000_000, 53, 0.05, 0.0)
+    gkref = gk.gk_load_reference(ref)
+    pool = serve.RequestPool(ref, lengths=(100, 150), reads_per_len=20_000, stride_words=None, keep_ascii=True,
+                             sequential=True, pair_format="starts", compact_reads=True)
+    cfg = serve.ServeConfig(mem_cap_bytes=1 << 30, max_round_pairs=500_000, lanes=(4, 5), pair_format="starts")
+    reqs = requests(pool, 120, 20_000.0, 66, size_hi=40_000, lengths=(100, 150))
+    assert all(r.nflag is None and r.lens is None for r in reqs)
+    srv = serve.Server(serve.GpuExecutor(gkref, cfg), cfg)
+    srv.run(reqs)
+    assert all(r.status == "done" for r in reqs)
+    for r in reqs[::4]:
+        a, e = oracle_of(ref, r)
+        assert np.array_equal(a, r.accept) and np.array_equal(e, r.edits), r.id
 
 
 def test_expand_pairs_writes_every_pair_once():
@@ -128,15 +154,32 @@ def test_expand_pairs_writes_every_pair_once():
     d = lambda a, dt: torch.from_numpy(np.asarray(a).astype(dt)).cuda()  # noqa: E731
     pread = torch.zeros(p_tot, dtype=torch.int32, device="cuda")
     pe = torch.zeros(p_tot, dtype=torch.uint8, device="cuda")
+    # per segment: a shared length (or 0: given per read) and / or "no N"
+    info = np.array([(int(rng.integers(1, 300)) if i % 3 else 0) | (gk.GK_SEG_NO_N if i % 2 else 0)
+                     for i in range(len(seg_e))], np.uint32)
+    lens = torch.full((n_rows,), 7, dtype=torch.int16, device="cuda")
+    nfl = torch.full((n_rows,), 9, dtype=torch.uint8, device="cuda")
     gk.gk_expand_pairs(pread, pe, d(read_start.view(np.int32), np.int32), d(seg_read_end, np.int64),
                        d(seg_pair_end, np.int64), d(seg_slot, np.int64),
                        d(np.array(seg_base, np.uint64).astype(np.uint32).view(np.int32), np.int32),
-                       d(seg_e, np.uint8), n_reads=r_tot)
+                       d(seg_e, np.uint8), n_reads=r_tot, seg_read_info=d(info.view(np.int32), np.int32),
+                       read_len=lens, read_nflag=nfl)
     torch.cuda.synchronize()
     got = pread.cpu().numpy().view(np.uint32)
     assert np.array_equal(got, want_id)
     claimed = want_id != 0xFFFFFFFF
     assert np.array_equal(pe.cpu().numpy()[claimed], want_e[claimed])
+    want_len = np.full(n_rows, 7, np.int16)
+    want_nf = np.full(n_rows, 9, np.uint8)
+    r0 = 0
+    for i, (re_, sl) in enumerate(zip(seg_read_end, seg_slot)):
+        rows = slice(sl, sl + re_ - r0)
+        if info[i] & 0xFFFF:
+            want_len[rows] = info[i] & 0xFFFF
+        if info[i] & gk.GK_SEG_NO_N:
+            want_nf[rows] = 0
+        r0 = re_
+    assert np.array_equal(lens.cpu().numpy(), want_len) and np.array_equal(nfl.cpu().numpy(), want_nf)
 
 
 def test_lanes_merged_copies_equal_the_oracle(setup):

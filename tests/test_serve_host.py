@@ -77,7 +77,8 @@ class FakeExecutor:
         for r in batch:
             rows = np.ascontiguousarray(r.ascii).reshape(-1)
             starts = np.arange(r.n_reads, dtype=np.uint64) * np.uint64(r.ascii.shape[1])
-            a, e, _ = O.filter_batch(rows, starts, r.lens, self.genome, ids_of(r), r.pair_off, r.e)
+            lens = r.lens if r.lens is not None else np.full(r.n_reads, r.read_len, np.uint16)
+            a, e, _ = O.filter_batch(rows, starts, lens, self.genome, ids_of(r), r.pair_off, r.e)
             self.out[r.id] = (a, e)
         return self.now + self.delay
 
@@ -313,3 +314,34 @@ def test_read_starts_requests_validate_continue_and_serve():
         want = O.filter_batch(rows, starts, r.lens, ref, (np.arange(r.n_pairs) // 4).astype(np.uint32),
                               r.pair_off, r.e)
         assert np.array_equal(want[0], r.accept) and np.array_equal(want[1], r.edits)
+
+
+def test_compact_read_descriptions():
+    """A starts-form request may give one read length instead of per-read
+    lengths and leave out the N flags when no read holds an N: the pool
+    does so per cut (flags kept where a read has an N), the per-segment word
+    for the device says which, and ids-form requests must give both."""
+    ref = synth.reference(300_000, 23, 0.05, 0.002)
+    pool = serve.RequestPool(ref, lengths=(100,), reads_per_len=3000, stride_words=4, pin=False,
+                             keep_ascii=True, sequential=True, pair_format="starts", compact_reads=True)
+    reqs = [pool.request(i, 100, 2, 40, 0, 0.0) for i in range(60)]
+    assert all(r.lens is None and r.read_len == 100 and r.max_len == 100 for r in reqs)
+    with_n = [r for r in reqs if r.nflag is not None]
+    without = [r for r in reqs if r.nflag is None]
+    assert with_n and without
+    for r in with_n:
+        assert r.nflag.any() and r.read_info == 100
+    for r in without:
+        assert not pool.by_len[100]["nflag"][1][r.start_base // 4:r.start_base // 4 + r.n_reads].any()
+        assert r.read_info == 100 | 0x10000
+    a = reqs[0]
+    with pytest.raises(ValueError):
+        serve.Request(9, a.packed, None, None, np.zeros(a.n_pairs, np.uint32), a.pair_off, 3, read_len=100)
+    with pytest.raises(ValueError):
+        serve.Request(9, a.packed, None, None, None, a.pair_off, 3, read_start=a.read_start)
+    with pytest.raises(ValueError):
+        serve.RequestPool(ref, lengths=(100,), reads_per_len=100, pin=False, compact_reads=True)
+    ex = FakeExecutor(ref, 100_000, 400_000)
+    srv = serve.Server(ex, serve.ServeConfig(stride_words=4, max_read_len=128, pair_format="starts"))
+    srv.run(reqs, clock=SimClock(ex), idle_sleep=0)
+    assert all(r.status == "done" for r in reqs)
