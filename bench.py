@@ -830,7 +830,11 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
     every window listed beside it."""
     dev = torch.device("cuda", torch.cuda.current_device())
     h_asc = torch.from_numpy(w.reads).pin_memory()
-    h_pr = dd.as_i32(w.pair_read).pin_memory()
+    # The candidates of a read sit side by side: they travel as one start per
+    # read (GK_PIPE_READ_STARTS) instead of a read id per pair.
+    starts = bool(np.all(np.diff(w.pair_read.astype(np.int64)) >= 0))
+    link = np.searchsorted(w.pair_read, np.arange(w.n_reads)).astype(np.uint32) if starts else w.pair_read
+    h_pr = dd.as_i32(link).pin_memory()
     h_po = dd.as_i32(w.pair_off).pin_memory()
     n = w.n_pairs
     slots = 3
@@ -838,7 +842,7 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
              None if result_byte else torch.empty(len(E_SWEEP) * n, dtype=torch.int16).pin_memory())
             for _ in range(slots)]
     pipe = gk.Pipe(ref, w.n_reads, w.stride, m, n, E_SWEEP, n_slots=slots,
-                   flags=gk.GK_FLAG_RESULT_BYTE if result_byte else 0)
+                   flags=(gk.GK_FLAG_RESULT_BYTE if result_byte else 0) | (gk.GK_PIPE_READ_STARTS if starts else 0))
 
     def run(k_steps):
         tickets = []
@@ -874,7 +878,7 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
         windows.append(reduce_max(wall_ms, world, dev))
     ms = statistics.median(windows)
     pipe.close()
-    h2d = h_asc.numel() + 4 * n * 2
+    h2d = h_asc.numel() + 4 * n + 4 * h_pr.numel()
     d2h = len(E_SWEEP) * n * (1 if result_byte else 3)
     fmt = ("one result byte per pair and threshold (count capped at 253 or a sentinel; accept = byte <= e "
            "or undefined)" if result_byte else "accept byte + 16-bit count per pair and threshold")
@@ -887,6 +891,8 @@ def run_e2e(torch, gk, dd, w, ref, m, sw, stream, args, world, result_byte=True)
             "path": "pinned host ASCII reads + pairs -> gk_pipe (copy-in, device encode + one gk_filter_sweep "
                     "over the thresholds, copy-out on three streams, 3 steps in flight) -> results in pinned "
                     "host memory",
+            "pairs_in": ("offset per pair + one start per read (GK_PIPE_READ_STARTS)" if starts
+                         else "offset + read id per pair"),
             "results": fmt}
 
 

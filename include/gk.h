@@ -509,6 +509,9 @@ typedef struct gk_pipe_s *gk_pipe_t;
 
 #define GK_PIPE_SLICED 4u /* pipe flag: run the sliced filter (gk_slice +
                              gk_filter_sliced_sweep) where it covers the pipe */
+#define GK_PIPE_READ_STARTS 8u /* pipe flag: gk_pipe_submit's pair_read holds
+                                  one start per read (CSR), not a read id per
+                                  pair */
 
 typedef struct {
   uint64_t max_reads;          /* reads per batch, at most (>= 1) */
@@ -519,7 +522,8 @@ typedef struct {
   const uint8_t *thresholds;   /* host, n_thresholds values of e (copied at creation) */
   int count_mode;              /* GK_COUNT_RUNS4 or GK_COUNT_POPCOUNT */
   uint32_t flags;              /* 0, GK_FLAG_NO_EDGE_FIX, GK_FLAG_RESULT_BYTE
-                                  (then every threshold <= 252), GK_PIPE_SLICED */
+                                  (then every threshold <= 252), GK_PIPE_SLICED,
+                                  GK_PIPE_READ_STARTS */
   uint32_t n_slots;            /* batches in flight, 2..4 */
 } gk_pipe_desc_t;
 
@@ -531,7 +535,11 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *desc, gk_pipe_t *out);
 /*
  * Enqueue one batch and return at once.
  *   ascii       host, n_reads * ascii_stride bytes (read i at i*ascii_stride)
- *   pair_read   host, n_pairs uint32 read ids (within this batch)
+ *   pair_read   host, n_pairs uint32 read ids (within this batch); with
+ *               GK_PIPE_READ_STARTS instead n_reads uint32 starts: read i's
+ *               candidates are pairs pair_read[i] .. pair_read[i+1]-1 (the
+ *               last read's through n_pairs-1), a quarter of the bytes at 4
+ *               candidates per read (a pair no read claims is invalid)
  *   pair_off    host, n_pairs uint32 reference offsets
  *   accept_out  host, n_thresholds * n_pairs uint8, threshold-major (the
  *               result bytes with GK_FLAG_RESULT_BYTE)

@@ -78,6 +78,11 @@ cudaError_t launch_encode_reads(const uint8_t *ascii, uint64_t ascii_stride,
                                 cudaStream_t stream);
 cudaError_t launch_encode_contig(const uint8_t *ascii, uint64_t n_bases, uint2 *hl,
                                  uint32_t *nbits, cudaStream_t stream);
+// Read ids of one batch's pairs from its reads' starts (serve_util.cu):
+// pairs start[i] .. start[i+1]-1 (the last read's through n_pairs-1) get id
+// i, clamped to [0, n_pairs); pairs no read claims get 0xFFFFFFFF.
+cudaError_t launch_expand_rows(uint32_t *pair_read, uint64_t n_pairs, const uint32_t *read_start,
+                               uint64_t n_reads, cudaStream_t stream);
 // Host encoder (multi-threaded).
 void host_encode_reads(const uint8_t *ascii, uint64_t ascii_stride, const uint16_t *lens,
                        uint16_t fixed_len, uint64_t n_seq, uint32_t *packed,

@@ -23,6 +23,7 @@ constexpr uint32_t kMaxThresholds = 64;
 struct Slot {
   uint8_t *ascii = nullptr;
   uint32_t *pair_read = nullptr;
+  uint32_t *read_start = nullptr;  // the batch's per-read starts (GK_PIPE_READ_STARTS)
   uint32_t *pair_off = nullptr;
   uint32_t *packed = nullptr;
   uint8_t *nflag = nullptr;
@@ -57,6 +58,7 @@ struct gk_pipe_s {
   std::vector<uint8_t> thresholds;
   int count_mode = GK_COUNT_RUNS4;
   uint32_t flags = 0;
+  bool read_starts = false;  // pairs name their reads by per-read starts (GK_PIPE_READ_STARTS)
   uint64_t sliced_cap = 0;  // > 0: every batch is sliced once and filtered by gk_filter_sliced
   cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
   Slot slot[kMaxSlots];
@@ -70,6 +72,7 @@ void release(gk_pipe_s *p) {
   for (Slot &s : p->slot) {
     cudaFree(s.ascii);
     cudaFree(s.pair_read);
+    cudaFree(s.read_start);
     cudaFree(s.pair_off);
     cudaFree(s.packed);
     cudaFree(s.nflag);
@@ -114,7 +117,7 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
     return gk::fail(GK_EINVAL, "gk_pipe_create: n_thresholds must be 1..64 with a threshold array");
   if (d->count_mode != GK_COUNT_RUNS4 && d->count_mode != GK_COUNT_POPCOUNT)
     return gk::fail(GK_EINVAL, "gk_pipe_create: unknown count_mode");
-  if (d->flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE | GK_PIPE_SLICED))
+  if (d->flags & ~(GK_FLAG_NO_EDGE_FIX | GK_FLAG_RESULT_BYTE | GK_PIPE_SLICED | GK_PIPE_READ_STARTS))
     return gk::fail(GK_EINVAL, "gk_pipe_create: unknown flags");
   if (d->flags & GK_FLAG_RESULT_BYTE)
     for (uint32_t i = 0; i < d->n_thresholds; ++i)
@@ -136,7 +139,8 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
   p->n_slots = d->n_slots;
   p->thresholds.assign(d->thresholds, d->thresholds + d->n_thresholds);
   p->count_mode = d->count_mode;
-  p->flags = d->flags & ~GK_PIPE_SLICED;  // the filters' flags
+  p->flags = d->flags & ~(GK_PIPE_SLICED | GK_PIPE_READ_STARTS);  // the filters' flags
+  p->read_starts = (d->flags & GK_PIPE_READ_STARTS) != 0;
   const uint64_t n_th = d->n_thresholds;
   // The bit-sliced filter when the pipe asks for it (GK_PIPE_SLICED) and it
   // covers the read length and every threshold (edge OR on, min(e, m-1)
@@ -152,6 +156,7 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *d, gk_pipe_t *out) {
   for (uint32_t i = 0; ok && i < p->n_slots; ++i) {
     Slot &s = p->slot[i];
     ok = alloc(&s.ascii, p->max_reads * p->ascii_stride) && alloc(&s.pair_read, 4 * p->max_pairs) &&
+         (!p->read_starts || alloc(&s.read_start, 4 * p->max_reads)) &&
          alloc(&s.pair_off, 4 * p->max_pairs) && alloc(&s.packed, 8ull * p->stride_words * p->max_reads) &&
          alloc(&s.nflag, p->max_reads) && alloc(&s.accept, n_th * p->max_pairs) &&
          ((p->flags & GK_FLAG_RESULT_BYTE) || alloc(&s.edits, 2 * n_th * p->max_pairs)) &&
@@ -196,10 +201,15 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
   if (n_reads && !cuda(cudaMemcpyAsync(s.ascii, ascii, n_reads * p->ascii_stride, cudaMemcpyHostToDevice, p->s_in),
                        "copy of the reads"))
     return p->sticky;
-  if (n_pairs && !(cuda(cudaMemcpyAsync(s.pair_read, pair_read, 4 * n_pairs, cudaMemcpyHostToDevice, p->s_in),
-                        "copy of the read ids") &&
-                   cuda(cudaMemcpyAsync(s.pair_off, pair_off, 4 * n_pairs, cudaMemcpyHostToDevice, p->s_in),
-                        "copy of the offsets")))
+  if (n_pairs &&
+      !((p->read_starts
+             ? (n_reads == 0 ||
+                cuda(cudaMemcpyAsync(s.read_start, pair_read, 4 * n_reads, cudaMemcpyHostToDevice, p->s_in),
+                     "copy of the read starts"))
+             : cuda(cudaMemcpyAsync(s.pair_read, pair_read, 4 * n_pairs, cudaMemcpyHostToDevice, p->s_in),
+                    "copy of the read ids")) &&
+        cuda(cudaMemcpyAsync(s.pair_off, pair_off, 4 * n_pairs, cudaMemcpyHostToDevice, p->s_in),
+             "copy of the offsets")))
     return p->sticky;
   if (!cuda(cudaEventRecord(s.in_done, p->s_in), "event")) return p->sticky;
   // run
@@ -210,6 +220,9 @@ int gk_pipe_submit(gk_pipe_t p, const uint8_t *ascii, uint64_t n_reads, const ui
                              p->stride_words, s.nflag, 1, p->s_run);
     if (rc != GK_OK) return broken(p, rc, std::string("gk_pipe_submit: ") + gk_last_error());
   }
+  if (p->read_starts && n_pairs &&
+      !cuda(gk::launch_expand_rows(s.pair_read, n_pairs, s.read_start, n_reads, p->s_run), "read ids from the starts"))
+    return p->sticky;
   if (p->sliced_cap && n_pairs) {
     const int rc = gk_slice(p->ref, s.packed, p->stride_words, n_reads, s.nflag, p->read_len, s.pair_read,
                             s.pair_off, n_pairs, s.sliced, p->sliced_cap, nullptr, p->s_run);

@@ -64,7 +64,33 @@ __global__ void expand_kernel(uint32_t *__restrict__ pair_read, uint8_t *__restr
   }
 }
 
+// One batch, one thread per read: pairs read_start[i] .. read_start[i+1]-1
+// (the last read's through n_pairs-1) get id i, clamped to the batch.
+__global__ void expand_rows_kernel(uint32_t *__restrict__ pair_read, uint64_t n_pairs,
+                                   const uint32_t *__restrict__ read_start, uint64_t n_reads) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n_reads) return;
+  const uint64_t a = read_start[i], b = i + 1 < n_reads ? (uint64_t)read_start[i + 1] : n_pairs;
+  const uint64_t to = b < n_pairs ? b : n_pairs;
+  for (uint64_t j = a; j < to; ++j) pair_read[j] = (uint32_t)i;
+}
+
 }  // namespace
+
+namespace gk {
+
+cudaError_t launch_expand_rows(uint32_t *pair_read, uint64_t n_pairs, const uint32_t *read_start, uint64_t n_reads,
+                               cudaStream_t stream) {
+  if (n_pairs == 0) return cudaSuccess;
+  cudaError_t err = cudaMemsetAsync(pair_read, 0xFF, n_pairs * sizeof(uint32_t), stream);
+  if (err != cudaSuccess || n_reads == 0) return err;
+  const int threads = 256;
+  expand_rows_kernel<<<(unsigned)((n_reads + threads - 1) / threads), threads, 0, stream>>>(pair_read, n_pairs,
+                                                                                          read_start, n_reads);
+  return cudaGetLastError();
+}
+
+}  // namespace gk
 
 extern "C" int gk_expand_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs, const uint32_t *read_start,
                                const uint64_t *seg_read_end, const uint64_t *seg_pair_end,

@@ -20,6 +20,7 @@ GK_COUNT_RUNS4, GK_COUNT_POPCOUNT = 0, 1
 GK_FLAG_NO_EDGE_FIX = 1
 GK_FLAG_RESULT_BYTE = 2
 GK_PIPE_SLICED = 4
+GK_PIPE_READ_STARTS = 8
 GK_RESULT_MAX_COUNT, GK_RESULT_UNDEFINED, GK_RESULT_INVALID = 253, 254, 255
 GK_EDITS_UNDEFINED, GK_EDITS_INVALID = 0xFFFF, 0xFFFE
 
@@ -597,13 +598,17 @@ class Pipe:
         self.ascii_stride = ascii_stride
         self.n_thresholds = int(th.size)
         self.result_byte = bool(flags & GK_FLAG_RESULT_BYTE)
+        self.read_starts = bool(flags & GK_PIPE_READ_STARTS)
         self._held = {}
 
     def submit(self, ascii, n_reads: int, pair_read, pair_off, accept_out, edits_out) -> int:
-        n_pairs = int(pair_read.shape[0]) if pair_read is not None else 0
+        """pair_read: a read id per pair, or with GK_PIPE_READ_STARTS one
+        start per read (read i's pairs are pair_read[i] .. pair_read[i+1]-1)."""
+        n_pairs = int(pair_off.shape[0]) if pair_off is not None else 0
         i32 = (torch.int32,)
+        n_link = n_reads if self.read_starts else n_pairs
         args = (_hptr(ascii, (torch.uint8,), "ascii", n_reads * self.ascii_stride), n_reads,
-                _hptr(pair_read, i32, "pair_read", n_pairs), _hptr(pair_off, i32, "pair_off", n_pairs), n_pairs,
+                _hptr(pair_read, i32, "pair_read", n_link), _hptr(pair_off, i32, "pair_off", n_pairs), n_pairs,
                 _hptr(accept_out, (torch.uint8,), "accept_out", self.n_thresholds * n_pairs),
                 None if self.result_byte else
                 _hptr(edits_out, (torch.int16,), "edits_out", self.n_thresholds * n_pairs))

@@ -31,12 +31,14 @@ def pinned(a: np.ndarray) -> torch.Tensor:
 
 @pytest.mark.parametrize("n_slots,ths,flags", [(2, THRESHOLDS, 0), (3, THRESHOLDS, 0), (4, THRESHOLDS, 0),
                                                (3, (1, 12), 0), (3, (0, 1, 2, 5, 6, 7, 29, 30, 31, 40), 0),
-                                               (3, THRESHOLDS, 4), (2, (1, 12), 4)])
+                                               (3, THRESHOLDS, 4), (2, (1, 12), 4), (3, THRESHOLDS, 8),
+                                               (2, (1, 12), 12)])
 def test_pipe_batches_equal_the_oracle(n_slots, ths, flags):
     """Runs of consecutive thresholds take one gk_filter_sweep each (shift
     counts up to 30), thresholds above it gk_filter; with GK_PIPE_SLICED
     (flags 4) gk_slice + gk_filter_sliced_sweep where the sliced filter
-    covers the set, gk_filter otherwise."""
+    covers the set, gk_filter otherwise; with GK_PIPE_READ_STARTS (flags 8)
+    the pairs' reads travel as one start per read."""
     require_gpu()
     THRESHOLDS = ths
     w = synth.config2(scale=0.001, ref_bases=2_000_000)
@@ -51,7 +53,11 @@ def test_pipe_batches_equal_the_oracle(n_slots, ths, flags):
         for asc, nr, pr, po, idx in bs:
             acc = torch.empty(len(THRESHOLDS) * pr.size, dtype=torch.uint8).pin_memory()
             ed = torch.empty(len(THRESHOLDS) * pr.size, dtype=torch.int16).pin_memory()
-            t = pipe.submit(pinned(asc), nr, pinned(pr), pinned(po), acc, ed)
+            link = pr
+            if flags & gk.GK_PIPE_READ_STARTS:  # the batch's pairs are grouped by read
+                assert np.all(np.diff(pr.astype(np.int64)) >= 0)
+                link = np.searchsorted(pr, np.arange(nr)).astype(np.uint32)
+            t = pipe.submit(pinned(asc), nr, pinned(link), pinned(po), acc, ed)
             jobs.append((t, acc, ed, idx))
         assert [j[0] for j in jobs] == list(range(len(bs)))
         pipe.wait(jobs[-1][0])  # the last ticket covers every earlier one
