@@ -536,9 +536,12 @@ __device__ __forceinline__ void deferred_sweep_counts(const FilterArgs &a, uint3
 // both ends before they are limited to the positions of a shift count.
 template <int NP>
 struct FinishPrep {
-  uint32_t q0[NP], qm[NP];
-  uint32_t lx[NP], ly[NP];  // low end: bit p set where a correction clears position p (from mask p) / p+1 (mask p)
-  uint32_t hx[NP], hy[NP];  // high end, mirrored (bit j: position m-1-j), bit-reversed
+  // The AND one base below position 0 is 1 at shift count K iff K < t0 (t0:
+  // the number of trailing 1s of the compare of window base 0 with the
+  // read's first bases); likewise above m-1 with tm.
+  uint32_t t0[NP], tm[NP];
+  uint32_t lx[NP], ly[NP];  // low end: bit p set where a correction clears position p (from mask p) / p+1 (mask p-1)
+  uint32_t hx[NP], hy[NP];  // high end, mirrored (bit j: position m-1-j), bit-reversed; hy pre-shifted by 1
 };
 
 // The high-end words are kept bit-reversed, so that each finish reverses one
@@ -559,16 +562,16 @@ __device__ __forceinline__ void deferred_prep(int j, uint32_t tail, uint32_t las
   {
     // Window base 0 against R[i] (bit i), every non-positive shift.
     const uint32_t g0h = 0u - (gh[j][0] & 1u), g0l = 0u - (gl[j][0] & 1u);
-    pr.q0[j] = (rh[0] ^ g0h) | (rl[0] ^ g0l);
+    pr.t0[j] = __ffs(~((rh[0] ^ g0h) | (rl[0] ^ g0l))) - 1u;  // 0xFFFFFFFF (all 1s): every K
     // The window's last 32 bases mirrored.
     const uint32_t mgh = __brev(__funnelshift_rc(W >= 2 ? gh[j][W >= 2 ? W - 2 : 0] : 0u, gh[j][W - 1], tail));
     const uint32_t mgl = __brev(__funnelshift_rc(W >= 2 ? gl[j][W >= 2 ? W - 2 : 0] : 0u, gl[j][W - 1], tail));
     // Window base m-1 against R[m-1-i] (bit i), every non-negative shift;
     // used only when m fills the words.
-    pr.qm[j] = 0u;
+    pr.tm[j] = 0u;
     if (tail == 32) {
       const uint32_t gmh = 0u - (mgh & 1u), gml = 0u - (mgl & 1u);
-      pr.qm[j] = (__brev(xrh) ^ gmh) | (__brev(xrl) ^ gml);
+      pr.tm[j] = __ffs(~((__brev(xrh) ^ gmh) | (__brev(xrl) ^ gml))) - 1u;
     }
     {  // low end (positions 1..K+1, word 0)
       const uint32_t v0 = W == 1 ? lastmask : 0xffffffffu;
@@ -578,7 +581,7 @@ __device__ __forceinline__ void deferred_prep(int j, uint32_t tail, uint32_t las
       const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
       const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
       pr.lx[j] = ~(c1 & c2);
-      pr.ly[j] = ~c2;
+      pr.ly[j] = ~c2 << 1;  // applied one position up
     }
     {  // high end (positions m-K-2..m-2), mirrored; kept bit-reversed
       const uint32_t a0 = (mgh ^ b0h) | (mgl ^ b0l);
@@ -587,7 +590,7 @@ __device__ __forceinline__ void deferred_prep(int j, uint32_t tail, uint32_t las
       const uint32_t c1 = (vac << 2) | (vac << 1) | a0;
       const uint32_t c2 = (vac << 1) | a0 | (a1 >> 1);
       pr.hx[j] = __brev(~(c1 & c2));
-      pr.hy[j] = __brev(~c2);
+      pr.hy[j] = __brev(~c2) >> 1;  // applied one position down (mirrored)
     }
   }
 }
@@ -601,35 +604,33 @@ __device__ __forceinline__ void deferred_finish(const FilterArgs &a, uint32_t K,
                                                 uint32_t lastmask, const uint32_t (&acc)[NP][W],
                                                 const FinishPrep<NP> &pr, uint32_t (&count)[NP]) {
   // ---- once per pair: end values of the AND, corrections, final erosion ----
-  const uint32_t rangeK = (2u << K) - 1u;  // bits 0..K
-  const uint32_t r1k = rangeK & ~1u;       // bits 1..K
-  const uint32_t r1kr = __brev(r1k);       // the same, mirrored
+  const uint32_t r1k = (2u << K) - 2u;  // bits 1..K
+  const uint32_t r2k = r1k << 1;         // bits 2..K+1
+  const uint32_t r1kr = __brev(r1k);     // bits 1..K, mirrored
+  const uint32_t r2kr = r1kr >> 1;       // bits 2..K+1, mirrored
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    // AND one base below position 0: every non-positive shift compares G[0]
-    // with R[i], i = 0..K.
-    const uint32_t vlo = ((~pr.q0[j] & rangeK) == 0) ? 1u : 0u;
-    // AND one base above position m-1, needed only when m fills the words:
-    // every non-negative shift compares G[m-1] with R[m-1-i], i = 0..K.
-    uint32_t vtop = 0u;
-    if (tail == 32) vtop = ((~pr.qm[j] & rangeK) == 0) ? 1u : 0u;
+    // AND one base below position 0 (every non-positive shift compares G[0]
+    // with R[i], i = 0..K) and, when m fills the words, above m-1.
+    const uint32_t lo0 = K < pr.t0[j] ? 0x80000000u : 0u;
+    const uint32_t vtop = (tail == 32 && K < pr.tm[j]) ? 1u : 0u;
     uint32_t f[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const uint32_t lo_in = w > 0 ? acc[j][w - 1] : (vlo << 31);
+      const uint32_t lo_in = w > 0 ? acc[j][w - 1] : lo0;
       const uint32_t hi_in = w + 1 < W ? acc[j][w + 1] : vtop;
       f[w] = acc[j][w] & __funnelshift_l(lo_in, acc[j][w], 1) & __funnelshift_r(acc[j][w], hi_in, 1);
     }
     // Low-end corrections (positions 1..K+1, word 0).
-    f[0] &= ~((pr.lx[j] & r1k) | ((pr.ly[j] & r1k) << 1));
+    f[0] &= ~((pr.lx[j] & r1k) | (pr.ly[j] & r2k));
     // High-end corrections (positions m-K-2..m-2), mapped back from the
-    // mirrored words: bit b of nc is position m-32+b.
+    // mirrored words: bit b of nc is position m-32+b; the last word also
+    // drops the positions past m.
     {
-      const uint32_t nc = (pr.hx[j] & r1kr) | ((pr.hy[j] & r1kr) >> 1);
-      f[W - 1] &= ~(nc >> (32u - tail));
+      const uint32_t nc = (pr.hx[j] & r1kr) | (pr.hy[j] & r2kr);
+      f[W - 1] &= ~(nc >> (32u - tail)) & lastmask;
       if (W >= 2 && tail < 32) f[W >= 2 ? W - 2 : 0] &= ~(nc << tail);
     }
-    f[W - 1] &= lastmask;
 
     uint32_t c = 0;
     if (a.count_mode == GK_COUNT_POPCOUNT) {
