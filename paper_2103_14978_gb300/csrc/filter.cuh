@@ -1036,8 +1036,20 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
       // 4-byte store per threshold when the rows keep that alignment.
       const bool pack = (((uintptr_t)a.accept | (a.result_byte ? 0u : (uintptr_t)a.edits)) & 3u) == 0 &&
                         (a.out_stride & 1u) == 0;
+      // The common case (K in e_lo..e_hi, below m-1) writes one row: its
+      // accept and count pointers advance by a row per shift count.
+      uint8_t *acc_row = a.accept + p0;
+      uint16_t *ed_row = a.edits + p0;
       deferred_sweep_counts<W, 2>(a, a.m, min(e_hi, kmax), rh, rl, gh, gl, count, min(e_lo, kmax),
                                   [&](uint32_t K, const uint32_t (&c)[2]) {
+                                    if (pack && !a.result_byte && K >= e_lo && K < kmax) {
+                                      *reinterpret_cast<uint32_t *>(ed_row) = c[0] | (c[1] << 16);
+                                      *reinterpret_cast<uint16_t *>(acc_row) =
+                                          (uint16_t)((c[0] <= K ? 1u : 0u) | (c[1] <= K ? 0x100u : 0u));
+                                      acc_row += a.out_stride;
+                                      ed_row += a.out_stride;
+                                      return;
+                                    }
                                     const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
                                     for (uint32_t e = first; e <= last; ++e) {
                                       const uint64_t o = (uint64_t)(e - e_lo) * a.out_stride;
