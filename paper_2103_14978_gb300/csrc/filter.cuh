@@ -128,17 +128,24 @@ __device__ __forceinline__ void load_words_wide(const uint2 *reads, uint32_t str
 }
 
 // Window words off/32 .. off/32 + W of a valid pair in 8-byte loads: 40
-// contiguous bytes, two 32-byte sectors.  (A copy of the genome holding
-// overlapping word pairs, read in 16-byte loads, measured 13% slower at e = 0:
-// its three loads touch three sectors.)
-template <int W, bool WIDE>
+// contiguous bytes, two 32-byte sectors.  SKIP_LAST: word off/32 + W only
+// when the window reaches into it ((off mod 32) + m > 32W); otherwise its
+// bits land past m, where the planes are masked (at 100 bp 29 pairs in 32
+// skip it).  (A copy of the genome holding overlapping word pairs, read in
+// 16-byte loads, measured 13% slower at e = 0: its three loads touch three
+// sectors.)
+template <int W, bool WIDE, bool SKIP_LAST = false>
 __device__ __forceinline__ void load_window(const FilterArgs &a, PairData<W> &x) {
   if (WIDE) {
     load_window_wide<W>(a.ref_hl, x);
   } else {
     const uint2 *gp = a.ref_hl + (x.off >> 5);
 #pragma unroll
-    for (int w = 0; w <= W; ++w) x.g[w] = gp[w];
+    for (int w = 0; w < W; ++w) x.g[w] = gp[w];
+    if (SKIP_LAST)
+      x.g[W] = (x.off & 31u) + x.m > 32u * W ? gp[W] : make_uint2(0u, 0u);
+    else
+      x.g[W] = gp[W];
   }
 }
 
@@ -147,7 +154,7 @@ __device__ __forceinline__ void load_window(const FilterArgs &a, PairData<W> &x)
 // wide form measured 2-6% slower at 100 and 150 bp.  share (nullable): a
 // pair loaded before; when it is valid and has the same read, its read words
 // and N flag are copied instead of loaded again.
-template <int W, bool WIDE = false>
+template <int W, bool WIDE = false, bool SKIP_LAST = false>
 __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairData<W> &x,
                                           const PairData<W> *share = nullptr) {
   x.rid = a.pair_read[p];
@@ -173,7 +180,7 @@ __device__ __forceinline__ void load_pair(const FilterArgs &a, uint64_t p, PairD
         for (int w = 0; w < W; ++w) x.r[w] = rp[w];
       }
     }
-    load_window<W, WIDE>(a, x);
+    load_window<W, WIDE, SKIP_LAST>(a, x);
   }
 }
 
@@ -976,8 +983,9 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks<W, COMPACT>::value) 
   }
 }
 
-// The two-pairs-per-thread kernel gathers in 8-byte loads: 16-byte loads
-// (load_words_wide) measured 4% slower at e = 0 and 1, 100 bp.
+// The two-pairs-per-thread kernel gathers in 8-byte loads except at a
+// compile-time shift count 0: 16-byte loads (load_words_wide) measured 2-4%
+// slower at every other shift count at 100 bp.
 constexpr bool kPair2Wide = false;
 
 // Resident blocks per SM of the two-pairs-per-thread kernel: 4 (64 registers,
@@ -1004,8 +1012,13 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
   const bool act0 = p0 < a.n_pairs, act1 = p1 < a.n_pairs;
   PairData<W> x0, x1;
   x0.status = x1.status = 0;
-  if (act0) load_pair<W, kPair2Wide>(a, p0, x0);
-  if (act1) load_pair<W, kPair2Wide>(a, p1, x1, act0 ? &x0 : nullptr);
+  // Shift count 0: read and window in 16-byte loads (e0 82.3 -> 85.4 Gpairs/s
+  // at 100 bp); 1 and 2: the window's last word loaded only when the window
+  // reaches into it (e1 68.2 -> 70.1, e2 58.7 -> 59.4); each measured slower
+  // with the other's choice.
+  constexpr bool kWide = kPair2Wide || KC == 0, kSkipLast = KC >= 1;
+  if (act0) load_pair<W, kWide, kSkipLast>(a, p0, x0);
+  if (act1) load_pair<W, kWide, kSkipLast>(a, p1, x1, act0 ? &x0 : nullptr);
   if (a.err_count) {
     const unsigned b0 = __ballot_sync(0xffffffffu, act0 && x0.status == 2);
     const unsigned b1 = __ballot_sync(0xffffffffu, act1 && x1.status == 2);
