@@ -1086,8 +1086,17 @@ __global__ void __launch_bounds__(kFilterThreads, MinBlocks2<W>::value) filter_p
     } else {
       const uint32_t K = KC >= 0 ? (uint32_t)KC : min(a.fixed_e, a.m - 1);
       deferred_counts<W, 2, (KC >= 0)>(a, a.m, K, rh, rl, gh, gl, count);
-      write_count(a, p0, count[0], a.fixed_e);
-      write_count(a, p1, count[1], a.fixed_e);
+      // The two pairs are adjacent: one 2-byte accept store and one 4-byte
+      // count store when the buffers allow it.
+      if (!a.result_byte && ((uintptr_t)a.accept & 1u) == 0 && ((uintptr_t)a.edits & 3u) == 0) {
+        const uint32_t e = a.fixed_e;
+        *reinterpret_cast<uint32_t *>(a.edits + p0) = count[0] | (count[1] << 16);
+        *reinterpret_cast<uint16_t *>(a.accept + p0) =
+            (uint16_t)((count[0] <= e ? 1u : 0u) | (count[1] <= e ? 0x100u : 0u));
+      } else {
+        write_count(a, p0, count[0], a.fixed_e);
+        write_count(a, p1, count[1], a.fixed_e);
+      }
     }
   } else {
     if (s0 == 0) filter_and_write<W, VARIANT>(a, p0, x0);
