@@ -744,7 +744,18 @@ __device__ __forceinline__ void sweep_and_write(const FilterArgs &a, uint64_t p,
   pair_planes<W>(x, rh, rl, gh[0], gl[0]);
   const uint32_t e_lo = a.fixed_e, e_hi = a.sweep_hi, kmax = x.m - 1;
   const uint32_t Klo = min(e_lo, kmax), Khi = min(e_hi, kmax);
+  // The common case (K in e_lo..e_hi, below m-1) writes one row: its
+  // pointers advance by a row per shift count.
+  uint8_t *acc_row = a.accept + p;
+  uint16_t *ed_row = a.edits + p;
   deferred_sweep_counts<W, 1>(a, x.m, Khi, rh, rl, gh, gl, count, Klo, [&](uint32_t K, const uint32_t (&c)[1]) {
+    if (!a.result_byte && K >= e_lo && K < kmax) {
+      *acc_row = c[0] <= K;
+      *ed_row = (uint16_t)c[0];
+      acc_row += a.out_stride;
+      ed_row += a.out_stride;
+      return;
+    }
     const uint32_t first = K > e_lo ? K : e_lo, last = K == kmax ? e_hi : K;
     for (uint32_t e = first; e <= last; ++e) write_count(a, p + (uint64_t)(e - e_lo) * a.out_stride, c[0], e);
   });
