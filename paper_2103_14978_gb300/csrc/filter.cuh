@@ -713,14 +713,18 @@ __device__ __forceinline__ int pair_status(const FilterArgs &a, const PairData<W
 template <bool SWEEP = false>
 __device__ __forceinline__ void write_trivial(const FilterArgs &a, uint64_t p, int status) {
   const uint32_t rows = SWEEP ? a.sweep_hi - a.fixed_e + 1 : 1;
-  for (uint32_t i = 0; i < rows; ++i) {
-    const uint64_t q = p + i * a.out_stride;
-    if (a.result_byte) {
-      a.accept[q] = status == 0 ? 0 : (status == 1 ? GK_RESULT_UNDEFINED : GK_RESULT_INVALID);
-      continue;
-    }
-    a.accept[q] = status != 2;
-    a.edits[q] = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+  uint8_t *acc = a.accept + p;
+  if (a.result_byte) {
+    const uint8_t b = status == 0 ? 0 : (status == 1 ? GK_RESULT_UNDEFINED : GK_RESULT_INVALID);
+    for (uint32_t i = 0; i < rows; ++i, acc += a.out_stride) *acc = b;
+    return;
+  }
+  uint16_t *ed = a.edits + p;
+  const uint8_t acc_v = status != 2;
+  const uint16_t ed_v = status == 0 ? 0 : (status == 1 ? GK_EDITS_UNDEFINED : GK_EDITS_INVALID);
+  for (uint32_t i = 0; i < rows; ++i, acc += a.out_stride, ed += a.out_stride) {
+    *acc = acc_v;
+    *ed = ed_v;
   }
 }
 
