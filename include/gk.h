@@ -398,9 +398,10 @@ int gk_rebase_pairs(uint32_t *pair_read, uint8_t *pair_e, uint64_t n_pairs,
  *                  such requests need not send these per-read arrays
  * Writes pair_read[j] = the row of the read owning pair j and pair_e[j] =
  * its segment's threshold.  Starts are clamped to the segment's pairs; a
- * pair that no read claims (starts decreasing or skipping pairs) gets id
- * 0xFFFFFFFF, which the filters report as an invalid pair.  Asynchronous on
- * `stream`.
+ * pair that no read claims (before the first read's start) gets id
+ * 0xFFFFFFFF, which the filters report as an invalid pair; with decreasing
+ * starts a pair may be claimed by two reads and gets one of them.
+ * Asynchronous on `stream`.
  */
 #define GK_SEG_NO_N 0x10000u
 
@@ -539,7 +540,9 @@ int gk_pipe_create(gk_ref_t ref, const gk_pipe_desc_t *desc, gk_pipe_t *out);
  *               GK_PIPE_READ_STARTS instead n_reads uint32 starts: read i's
  *               candidates are pairs pair_read[i] .. pair_read[i+1]-1 (the
  *               last read's through n_pairs-1), a quarter of the bytes at 4
- *               candidates per read (a pair no read claims is invalid)
+ *               candidates per read (pairs before the first read's start are
+ *               invalid; with decreasing starts a pair claimed by two reads
+ *               gets one of them)
  *   pair_off    host, n_pairs uint32 reference offsets
  *   accept_out  host, n_thresholds * n_pairs uint8, threshold-major (the
  *               result bytes with GK_FLAG_RESULT_BYTE)

@@ -139,3 +139,33 @@ def test_pipe_result_bytes_equal_the_oracle():
     with pytest.raises(gk.GKError):
         gk.Pipe(ref, 10, w.stride, 100, 10, (3, 253), flags=gk.GK_FLAG_RESULT_BYTE)
     ref.close()
+
+
+def test_pipe_read_starts_leave_unclaimed_pairs_invalid():
+    """GK_PIPE_READ_STARTS with starts that skip pairs (the first read starts
+    at 3, so no read claims pairs 0..2): claimed pairs equal the oracle,
+    unclaimed pairs come back invalid (accept 0, GK_EDITS_INVALID; result
+    byte GK_RESULT_INVALID)."""
+    require_gpu()
+    w = synth.config2(scale=0.0002, ref_bases=2_000_000)
+    ref = gk.gk_load_reference(w.ref)
+    (asc, nr, pr, po, idx), = batches_of(w, [0, 600])
+    starts = np.searchsorted(pr, np.arange(nr)).astype(np.uint32)
+    assert starts[0] == 0 and starts[1] >= 4
+    starts[0] = 3
+    claimed = np.arange(pr.size) >= 3
+    want = oracle_run(w, 4)
+    for flags in (gk.GK_PIPE_READ_STARTS, gk.GK_PIPE_READ_STARTS | gk.GK_FLAG_RESULT_BYTE):
+        with gk.Pipe(ref, nr, w.stride, 100, pr.size, (4,), flags=flags) as pipe:
+            acc = torch.empty(pr.size, dtype=torch.uint8).pin_memory()
+            ed = torch.empty(pr.size, dtype=torch.int16).pin_memory()
+            pipe.wait(pipe.submit(pinned(asc), nr, pinned(starts), pinned(po), acc, ed))
+            a = acc.numpy()
+            if flags & gk.GK_FLAG_RESULT_BYTE:
+                assert np.all(a[~claimed] == gk.GK_RESULT_INVALID)
+                assert np.array_equal(a[claimed], _result_bytes_of(want[0][idx][claimed], want[1][idx][claimed]))
+            else:
+                d = ed.numpy().view(np.uint16)
+                assert np.all(a[~claimed] == 0) and np.all(d[~claimed] == gk.GK_EDITS_INVALID)
+                assert_same((a[claimed], d[claimed]), (want[0][idx][claimed], want[1][idx][claimed]), "claimed")
+    ref.close()
